@@ -1,0 +1,174 @@
+/*
+ * hartree.h -- C ABI of the GB300 (sm_103a) grid-side Hartree step.
+ *
+ * The operation is the Hartree part of the Kohn-Sham potential and energy of
+ * Duy & Ozaki, arXiv:1209.4506: Sec. 2.1, Eq. Hartree-potential (the
+ * potential of the density) and the E_Hartree term of Eq. total-energy, with
+ * the potential "found by solving the Poisson equation using FFT" (Sec. 2.1)
+ * in the transform order abc -> cab -> cba -> cab -> abc of Sec. 3.2.4.
+ *
+ * Conventions shared by every entry point
+ *   Units       atomic units: Bohr, Hartree, charge in e.  V_H > 0 near a
+ *               positive charge (V_H solves lap V = -4 pi rho).
+ *   Cell        orthorhombic, sides L = (L1, L2, L3), volume Omega = L1 L2 L3.
+ *   Grid        N = (N1, N2, N3) points along a, b, c; point (i, j, k) sits at
+ *               (i L1/N1, j L2/N2, k L3/N3); arrays are C order [N1][N2][N3],
+ *               c fastest (the paper's structure B "abc" layout).  dV = Omega/N.
+ *   Density     atom i is the Gaussian q_i (pi s^2)^(-3/2) exp(-|r - R_i|^2/s^2)
+ *               (s = sigma), summed over all periodic images, truncated per
+ *               axis at |x| <= cutoff_sigmas * sigma.
+ *   Poisson     V~(G) = 4 pi / |G|^2 rho~(G) for G != 0, V~(0) = 0 (uniform
+ *               neutralising background; a net charge is allowed).
+ *   Energy      E_H = 1/2 dV sum_r rho(r) V_H(r)   (FP64 on the device).
+ *   Forces      F_i = -dE_H/dR_i = -dV sum_r V_H(r) d rho_i(r)/dR_i   (FP64).
+ *   Precision   the element type of every void* grid buffer follows the plan:
+ *               HARTREE_FP64 -> double, HARTREE_FP32 -> float,
+ *               HARTREE_FP32_TC_SPLIT -> float.  Positions, charges, energies
+ *               and forces are always double.
+ *   Memory      "device" pointers are CUDA global memory of the current device,
+ *               owned by the caller.  The plan owns its workspace, allocated
+ *               once in hartree_plan_create; the per-solve calls allocate
+ *               nothing and only enqueue work on the given stream.
+ *   Streams     `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *               default stream).  Calls return once the work is enqueued; the
+ *               *_host entry points also wait for it.
+ *   Errors      every call returns a hartree_status; nothing aborts and no
+ *               C++ exception crosses the boundary.  hartree_last_error()
+ *               returns a thread-local message for the most recent failure.
+ *   Threads     a plan may be used from one host thread at a time.
+ */
+#ifndef HARTREE_H
+#define HARTREE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hartree_plan_s* hartree_plan;
+typedef struct hartree_batch_s* hartree_batch;
+
+typedef enum {
+    HARTREE_FP64 = 0,          /* FP64 transforms and grids                          */
+    HARTREE_FP32 = 1,          /* FP32 transforms and grids, FP64 E_H and forces      */
+    HARTREE_FP32_TC_SPLIT = 2  /* FP32, radix-16 stages on BF16 tensor cores (hi/lo) */
+} hartree_precision;
+
+typedef enum {
+    HARTREE_OK = 0,
+    HARTREE_ERR_INVALID = 1,          /* null pointer, bad count, sigma <= 0, NaN/Inf ... */
+    HARTREE_ERR_UNSUPPORTED_SIZE = 2, /* a grid size that is not 2/3/5-smooth, odd N3 ...  */
+    HARTREE_ERR_CUDA = 3,             /* a CUDA runtime call failed                        */
+    HARTREE_ERR_OOM = 4,              /* device allocation failed in a *_create call       */
+    HARTREE_ERR_TIMEOUT = 5,          /* a bounded device wait gave up (batched form)      */
+    HARTREE_ERR_NOT_CAPTURABLE = 6    /* the call cannot run under stream capture          */
+} hartree_status;
+
+typedef struct {
+    int n[3];             /* grid points N1, N2, N3; 2/3/5-smooth, 2 <= N_d <= 4096, N3 even >= 4 */
+    double cell[3];       /* L1, L2, L3 in Bohr, > 0                                        */
+    double sigma;         /* Gaussian width s in Bohr, > 0                                  */
+    double cutoff_sigmas; /* per-axis truncation radius in units of s; 0 = default
+                             (8 for FP64, 6 for FP32); must not exceed 16                   */
+    int precision;        /* a hartree_precision                                            */
+    int atoms_per_leaf;   /* atoms per bisection leaf used by the splat; 0 = default 16     */
+    int max_atoms;        /* largest atom count any call on this plan will pass; 0 = 65536 */
+    unsigned flags;       /* reserved, must be 0                                            */
+} hartree_desc;
+
+/* ---------------------------------------------------------------- plans */
+
+/*
+ * Validate `desc`, allocate the plan's device workspace (half spectrum,
+ * one real grid, twiddle and |G|^2 tables, reduction partials, leaf boxes)
+ * and upload the FP64-generated twiddle tables.  Uses the current device.
+ * desc: host pointer, read only.  out: host pointer receiving the plan.
+ * Returns HARTREE_ERR_UNSUPPORTED_SIZE for grids the transforms do not
+ * handle, HARTREE_ERR_OOM when the workspace does not fit.
+ */
+int hartree_plan_create(const hartree_desc* desc, hartree_plan* out);
+
+/* Free the plan and its workspace (synchronises the device first). NULL is a no-op. */
+void hartree_plan_destroy(hartree_plan plan);
+
+/* Bytes of device memory the plan holds. */
+unsigned long long hartree_plan_workspace_bytes(hartree_plan plan);
+
+/* ---------------------------------------------------------------- atom reorder */
+
+/*
+ * Modified recursive bisection with the inertia-tensor principal axis
+ * (Sec. 3.1.2-3.1.5; Eqs. center-of-mass, eq-projection-ti, eq-function-F,
+ * eq-inertia-tensor).  Host-side and FP64; run once per geometry (Step 1 of
+ * Sec. 4), not per solve.
+ *   pos        host [n][3] positions in Bohr (used as given, not wrapped)
+ *   w          host [n] weights (Eq. eq-weight-def) or NULL for all 1
+ *   n_leaves   number of leaves (the paper's process count), >= 1
+ *   perm       host [n] out: atom indices in leaf order
+ *   leaf_start host [n_leaves + 1] out: leaf l owns perm[leaf_start[l] ..
+ *              leaf_start[l + 1])
+ * Reading of the paper: the left child takes ceil(p/2) of p processes and the
+ * shortest prefix (by projection t) whose weight W_k satisfies
+ * p W_k >= ceil(p/2) W; the axis sign makes its largest component positive.
+ */
+int hartree_atoms_reorder(const double* pos, const double* w, int n, int n_leaves, int* perm, int* leaf_start);
+
+/* ---------------------------------------------------------------- single solves */
+
+/*
+ * Density splat (Sec. 3.2.2 structure A -> B): rho on the grid from n
+ * Gaussian charges.  Leaves are runs of atoms_per_leaf consecutive atoms; pass
+ * atoms in hartree_atoms_reorder order so each grid tile touches a few leaves
+ * (any order gives the same result up to rounding).
+ *   pos  device [n][3] double, Bohr, any values (periodic images are implied)
+ *   q    device [n] double
+ *   rho  device [N1][N2][N3] element type of the plan, out
+ * 0 <= n <= max_atoms.
+ */
+int hartree_splat(hartree_plan plan, const double* pos, const double* q, int n, void* rho, void* stream);
+
+/*
+ * Poisson solve of a density already on the grid: five passes c-r2c, b, a
+ * (forward, x 4 pi/|G|^2, E_H reduction, inverse), b^-1, c-c2r.
+ *   rho  device [N1][N2][N3], read only (may alias vh: then it is overwritten)
+ *   vh   device [N1][N2][N3], out
+ *   eh   device double scalar, out (may be NULL)
+ */
+int hartree_solve_density(hartree_plan plan, const void* rho, void* vh, double* eh, void* stream);
+
+/*
+ * Splat + Poisson solve + E_H.
+ *   rho  device [N1][N2][N3] out, or NULL (rho then lives in vh until V_H
+ *        overwrites it)
+ *   vh   device [N1][N2][N3] out;  eh device double out (may be NULL)
+ */
+int hartree_solve(hartree_plan plan, const double* pos, const double* q, int n, void* rho, void* vh, double* eh,
+                  void* stream);
+
+/*
+ * Adjoint gather: forces and charge derivatives from V_H.
+ *   vh   device [N1][N2][N3] potential of the same atoms, or NULL: then the
+ *        plan first solves into its own grid buffer (recompute, no extra memory)
+ *   f    device [n][3] double out, Ha/Bohr (F = -dE_H/dR)
+ *   phi  device [n] double out (dE_H/dq_i), may be NULL
+ */
+int hartree_forces(hartree_plan plan, const double* pos, const double* q, int n, const void* vh, double* f,
+                   double* phi, void* stream);
+
+/*
+ * End-to-end step on host buffers: copies pos and q to the device, runs
+ * splat, solve and forces with V_H kept in the plan's grid buffer, copies E_H
+ * (and forces when f is not NULL) back, and waits for the stream.
+ *   pos host [n][3], q host [n], eh host double out, f host [n][3] out or NULL.
+ */
+int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int n, double* eh, double* f,
+                      void* stream);
+
+/* ---------------------------------------------------------------- errors */
+
+const char* hartree_status_string(int status);
+const char* hartree_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HARTREE_H */

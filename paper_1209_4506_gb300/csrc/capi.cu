@@ -1,0 +1,356 @@
+// capi.cu -- plan creation and the extern "C" entry points of hartree.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace hartree;
+
+struct hartree_plan_s {
+    Plan p;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(HARTREE_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool smooth235(int n) {
+    if (n < 1) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Radices for a line of length n: powers of two in balanced stages of at
+// most 16, then the factors 3 and 5 one stage each.
+bool make_radix_plan(int n, RadixPlan* rp) {
+    rp->n = n;
+    rp->nst = 0;
+    int e2 = 0, m = n;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++e2;
+    }
+    int n3 = 0, n5 = 0;
+    while (m % 3 == 0) {
+        m /= 3;
+        ++n3;
+    }
+    while (m % 5 == 0) {
+        m /= 5;
+        ++n5;
+    }
+    if (m != 1) return false;
+    if (e2 > 0) {
+        const int st = (e2 + 3) / 4;
+        for (int s = 0; s < st; ++s) {
+            const int bits = e2 / st + (s < e2 % st ? 1 : 0);
+            rp->r[rp->nst++] = 1 << bits;
+        }
+    }
+    for (int i = 0; i < n3; ++i) rp->r[rp->nst++] = 3;
+    for (int i = 0; i < n5; ++i) rp->r[rp->nst++] = 5;
+    if (rp->nst == 0) rp->r[rp->nst++] = 2;  // n == 1 never reaches here (n >= 2)
+    return rp->nst <= kMaxStages;
+}
+
+// exp(-2 pi i k / n), k < n, evaluated in extended precision and rounded once.
+void twiddles(int n, std::vector<double>& re, std::vector<double>& im) {
+    re.resize(n);
+    im.resize(n);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int k = 0; k < n; ++k) {
+        const long double a = two_pi * (long double)k / (long double)n;
+        re[k] = (double)cosl(a);
+        im[k] = (double)(-sinl(a));
+    }
+}
+
+// (2 pi k' / L)^2 with k' = k for k <= n/2, k - n otherwise.
+std::vector<double> gsq_table(int n, int len, double L) {
+    std::vector<double> g(len);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < len; ++k) {
+        const int kk = (2 * k <= n) ? k : k - n;
+        const double G = two_pi * kk / L;
+        g[k] = G * G;
+    }
+    return g;
+}
+
+template <typename T>
+int upload_tables(Plan& p) {
+    for (int d = 0; d < 3; ++d) {
+        std::vector<double> re, im;
+        twiddles(p.n[d], re, im);
+        std::vector<T> buf(2 * (size_t)p.n[d]);
+        for (int k = 0; k < p.n[d]; ++k) {
+            buf[2 * k] = (T)re[k];
+            buf[2 * k + 1] = (T)im[k];
+        }
+        cudaError_t e = cudaMemcpy(p.tw[d], buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e) return cuda_fail(e, "upload twiddles");
+        const int len = d == 2 ? p.nh : p.n[d];
+        std::vector<double> g = gsq_table(p.n[d], len, p.L[d]);
+        std::vector<T> gb(g.begin(), g.end());
+        e = cudaMemcpy(p.gsq[d], gb.data(), gb.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e) return cuda_fail(e, "upload |G|^2 tables");
+    }
+    return HARTREE_OK;
+}
+
+void free_plan(Plan& p) {
+    void* ptrs[] = {p.W, p.R, p.tw[0], p.tw[1], p.tw[2], p.gsq[0], p.gsq[1], p.gsq[2], p.eh_partials,
+                    p.leaf_box, p.force_partials, p.d_pos, p.d_q, p.d_f, p.d_eh};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+bool finite_pos(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+extern "C" {
+
+const char* hartree_status_string(int status) {
+    switch (status) {
+        case HARTREE_OK: return "ok";
+        case HARTREE_ERR_INVALID: return "invalid argument";
+        case HARTREE_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+        case HARTREE_ERR_CUDA: return "CUDA error";
+        case HARTREE_ERR_OOM: return "out of device memory";
+        case HARTREE_ERR_TIMEOUT: return "device wait timed out";
+        case HARTREE_ERR_NOT_CAPTURABLE: return "not capturable";
+        default: return "unknown status";
+    }
+}
+
+const char* hartree_last_error(void) { return g_last_error.c_str(); }
+
+int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
+    if (!desc || !out) return fail(HARTREE_ERR_INVALID, "plan_create: null argument");
+    *out = nullptr;
+    const hartree_desc& d = *desc;
+    if (d.flags != 0) return fail(HARTREE_ERR_INVALID, "plan_create: flags must be 0");
+    if (d.precision != HARTREE_FP64 && d.precision != HARTREE_FP32 && d.precision != HARTREE_FP32_TC_SPLIT)
+        return fail(HARTREE_ERR_INVALID, "plan_create: unknown precision %d", d.precision);
+    if (d.precision == HARTREE_FP32_TC_SPLIT)
+        return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: HARTREE_FP32_TC_SPLIT is not available in this build");
+    for (int i = 0; i < 3; ++i) {
+        if (d.n[i] < 2 || d.n[i] > kMaxAxis || !smooth235(d.n[i]))
+            return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: N%d = %d is not a 2/3/5-smooth size in [2, %d]",
+                        i + 1, d.n[i], kMaxAxis);
+        if (!(d.cell[i] > 0.0) || !std::isfinite(d.cell[i]))
+            return fail(HARTREE_ERR_INVALID, "plan_create: cell[%d] must be positive and finite", i);
+    }
+    if (d.n[2] % 2 != 0 || d.n[2] < 4)
+        return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: N3 = %d must be even and >= 4", d.n[2]);
+    if (!(d.sigma > 0.0) || !std::isfinite(d.sigma)) return fail(HARTREE_ERR_INVALID, "plan_create: sigma must be > 0");
+    if (d.cutoff_sigmas < 0.0 || d.cutoff_sigmas > 16.0 || !std::isfinite(d.cutoff_sigmas))
+        return fail(HARTREE_ERR_INVALID, "plan_create: cutoff_sigmas must be in [0, 16]");
+    if (d.atoms_per_leaf < 0 || d.max_atoms < 0) return fail(HARTREE_ERR_INVALID, "plan_create: negative count");
+
+    hartree_plan_s* h = new (std::nothrow) hartree_plan_s();
+    if (!h) return fail(HARTREE_ERR_OOM, "plan_create: host allocation failed");
+    Plan& p = h->p;
+    p.desc = d;
+    p.prec = d.precision;
+    p.real_size = p.prec == HARTREE_FP64 ? sizeof(double) : sizeof(float);
+    for (int i = 0; i < 3; ++i) {
+        p.n[i] = d.n[i];
+        p.L[i] = d.cell[i];
+        p.h[i] = d.cell[i] / d.n[i];
+    }
+    p.M = p.n[2] / 2;
+    p.nh = p.M + 1;
+    {
+        const int align = p.prec == HARTREE_FP64 ? 8 : 16;  // 128-byte rows
+        p.ldc = (p.nh + align - 1) / align * align;
+    }
+    p.sigma = d.sigma;
+    p.rc = (d.cutoff_sigmas > 0.0 ? d.cutoff_sigmas : (p.prec == HARTREE_FP64 ? 8.0 : 6.0)) * d.sigma;
+    p.omega = p.L[0] * p.L[1] * p.L[2];
+    p.dV = p.omega / ((double)p.n[0] * p.n[1] * p.n[2]);
+    p.apl = d.atoms_per_leaf > 0 ? d.atoms_per_leaf : 16;
+    p.max_atoms = d.max_atoms > 0 ? d.max_atoms : 65536;
+    p.max_leaves = (p.max_atoms + p.apl - 1) / p.apl;
+    p.box_max = 0;
+    for (int i = 0; i < 3; ++i) {
+        const int c = (int)std::floor(2.0 * p.rc / p.h[i]) + 2;
+        if (c > p.box_max) p.box_max = c;
+    }
+    if (p.box_max > kMaxBoxPoints) {
+        delete h;
+        return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: cutoff box spans %d > %d grid points", p.box_max,
+                    kMaxBoxPoints);
+    }
+    for (int i = 0; i < 3; ++i) {
+        const int len = i == 2 ? p.M : p.n[i];
+        if (!make_radix_plan(len, &p.rp[i])) {
+            delete h;
+            return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: no radix plan for length %d", len);
+        }
+    }
+    // tiling: two ping-pong buffers per CTA, about 64 KB of shared memory
+    const size_t cs = 2 * p.real_size;  // complex element
+    const size_t budget = 64 * 1024;
+    p.c_lines = (int)(budget / (2 * (size_t)(p.M + 1) * cs)) - 1;
+    if (p.c_lines > 32) p.c_lines = 32;
+    if (p.c_lines < 2) p.c_lines = 2;
+    p.c_lines &= ~1;  // even, so the padded leading dimension L + 1 is odd
+    p.b_cols = (int)(budget / (2 * (size_t)p.n[1] * cs));
+    p.a_cols = (int)(budget / (2 * (size_t)p.n[0] * cs));
+    p.b_cols = p.b_cols > 16 ? 16 : (p.b_cols < 1 ? 1 : p.b_cols);
+    p.a_cols = p.a_cols > 16 ? 16 : (p.a_cols < 1 ? 1 : p.a_cols);
+    p.smem_c = 2 * (size_t)(p.M + 1) * (p.c_lines + 1) * cs;
+    p.smem_b = 2 * (size_t)p.n[1] * p.b_cols * cs;
+    p.smem_a = 2 * (size_t)p.n[0] * p.a_cols * cs;
+    const int a_chunks = (p.nh + p.a_cols - 1) / p.a_cols;
+    p.n_eh_partials = p.n[1] * a_chunks;
+    p.max_force_slabs = 1216;
+
+    const size_t ntot = (size_t)p.n[0] * p.n[1] * p.n[2];
+    struct Alloc {
+        void** ptr;
+        size_t bytes;
+    } allocs[] = {
+        {&p.W, (size_t)p.n[0] * p.n[1] * p.ldc * cs},
+        {&p.R, ntot * p.real_size},
+        {&p.tw[0], (size_t)p.n[0] * cs},
+        {&p.tw[1], (size_t)p.n[1] * cs},
+        {&p.tw[2], (size_t)p.n[2] * cs},
+        {&p.gsq[0], (size_t)p.n[0] * p.real_size},
+        {&p.gsq[1], (size_t)p.n[1] * p.real_size},
+        {&p.gsq[2], (size_t)p.nh * p.real_size},
+        {(void**)&p.eh_partials, (size_t)p.n_eh_partials * sizeof(double)},
+        {(void**)&p.leaf_box, (size_t)p.max_leaves * 6 * sizeof(double)},
+        {(void**)&p.force_partials, (size_t)(p.max_atoms + p.max_force_slabs) * 4 * sizeof(double)},
+        {(void**)&p.d_pos, (size_t)p.max_atoms * 3 * sizeof(double)},
+        {(void**)&p.d_q, (size_t)p.max_atoms * sizeof(double)},
+        {(void**)&p.d_f, (size_t)p.max_atoms * 3 * sizeof(double)},
+        {(void**)&p.d_eh, sizeof(double)},
+    };
+    for (auto& a : allocs) {
+        cudaError_t e = cudaMalloc(a.ptr, a.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_plan(p);
+            delete h;
+            return fail(e == cudaErrorMemoryAllocation ? HARTREE_ERR_OOM : HARTREE_ERR_CUDA,
+                        "plan_create: cudaMalloc(%zu bytes): %s", a.bytes, cudaGetErrorString(e));
+        }
+        p.bytes += a.bytes;
+    }
+    int st = p.prec == HARTREE_FP64 ? upload_tables<double>(p) : upload_tables<float>(p);
+    if (st == HARTREE_OK) {
+        cudaError_t e = configure_poisson_kernels(p);
+        if (e == cudaSuccess) e = configure_atom_kernels(p);
+        if (e != cudaSuccess) st = cuda_fail(e, "plan_create: kernel attributes");
+    }
+    if (st != HARTREE_OK) {
+        free_plan(p);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return HARTREE_OK;
+}
+
+void hartree_plan_destroy(hartree_plan plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    free_plan(plan->p);
+    delete plan;
+}
+
+unsigned long long hartree_plan_workspace_bytes(hartree_plan plan) { return plan ? plan->p.bytes : 0ULL; }
+
+int hartree_splat(hartree_plan plan, const double* pos, const double* q, int n, void* rho, void* stream) {
+    if (!plan || !rho || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "splat: null argument");
+    if (n < 0 || n > plan->p.max_atoms)
+        return fail(HARTREE_ERR_INVALID, "splat: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
+    cudaError_t e = launch_splat(plan->p, pos, q, n, rho, (cudaStream_t)stream);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "splat");
+}
+
+int hartree_solve_density(hartree_plan plan, const void* rho, void* vh, double* eh, void* stream) {
+    if (!plan || !rho || !vh) return fail(HARTREE_ERR_INVALID, "solve_density: null argument");
+    cudaError_t e = launch_poisson(plan->p, rho, vh, eh, (cudaStream_t)stream);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "solve_density");
+}
+
+int hartree_solve(hartree_plan plan, const double* pos, const double* q, int n, void* rho, void* vh, double* eh,
+                  void* stream) {
+    if (!plan || !vh || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "solve: null argument");
+    if (n < 0 || n > plan->p.max_atoms)
+        return fail(HARTREE_ERR_INVALID, "solve: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
+    void* dens = rho ? rho : vh;
+    cudaError_t e = launch_splat(plan->p, pos, q, n, dens, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = launch_poisson(plan->p, dens, vh, eh, (cudaStream_t)stream);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "solve");
+}
+
+int hartree_forces(hartree_plan plan, const double* pos, const double* q, int n, const void* vh, double* f,
+                   double* phi, void* stream) {
+    if (!plan || !f || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "forces: null argument");
+    if (n < 0 || n > plan->p.max_atoms)
+        return fail(HARTREE_ERR_INVALID, "forces: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!vh) {
+        e = launch_splat(plan->p, pos, q, n, plan->p.R, s);
+        if (e == cudaSuccess) e = launch_poisson(plan->p, plan->p.R, plan->p.R, nullptr, s);
+        vh = plan->p.R;
+    }
+    if (e == cudaSuccess) e = launch_forces(plan->p, pos, q, n, vh, f, phi, s);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "forces");
+}
+
+int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int n, double* eh, double* f,
+                      void* stream) {
+    if (!plan || !eh || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "step_host: null argument");
+    Plan& p = plan->p;
+    if (n < 0 || n > p.max_atoms)
+        return fail(HARTREE_ERR_INVALID, "step_host: n = %d outside [0, max_atoms = %d]", n, p.max_atoms);
+    for (int i = 0; i < 3 * n; ++i)
+        if (!finite_pos(pos[i])) return fail(HARTREE_ERR_INVALID, "step_host: position %d is not finite", i / 3);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "step_host");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(HARTREE_ERR_NOT_CAPTURABLE, "step_host waits for the stream; it cannot be captured");
+    if (n > 0) {
+        e = cudaMemcpyAsync(p.d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p.d_q, q, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = launch_splat(p, p.d_pos, p.d_q, n, p.R, s);
+    if (e == cudaSuccess) e = launch_poisson(p, p.R, p.R, p.d_eh, s);
+    if (e == cudaSuccess && f && n > 0) e = launch_forces(p, p.d_pos, p.d_q, n, p.R, p.d_f, nullptr, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(eh, p.d_eh, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && f && n > 0)
+        e = cudaMemcpyAsync(f, p.d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "step_host");
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+// fft_engine.cuh -- device building blocks of the line transforms of the
+// Poisson solve (Sec. 2.1: "the Hartree potential is found by solving the
+// Poisson equation using FFT"; pass order of Sec. 3.2.4).
+//
+// A tile is `ncol` independent lines of length N, all transformed together.
+// Stockham autosort stages (radix R, sub-transform size Ns) read butterfly j
+// at j + r N/R and write it at (j / Ns) Ns R + (j mod Ns) + r Ns, so every
+// stage reads with unit stride across butterflies and the output comes out in
+// natural order without a bit-reversal pass.  Threads run column-fastest:
+// neighbouring threads handle neighbouring columns, which are contiguous in
+// global memory for the b and a passes and in the [n][ld] shared-memory
+// layout, so loads, stores and shared-memory accesses are conflict-free.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hartree {
+
+template <typename T>
+struct __align__(2 * sizeof(T)) cpx {
+    T re, im;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> mk(T r, T i) {
+    cpx<T> z;
+    z.re = r;
+    z.im = i;
+    return z;
+}
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) {
+    return mk(a.re + b.re, a.im + b.im);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) {
+    return mk(a.re - b.re, a.im - b.im);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<T> b) {
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) {
+    return mk(a.re * s, a.im * s);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> conjg(cpx<T> a) {
+    return mk(a.re, -a.im);
+}
+// a * (-i) for the forward sign, a * (+i) for the inverse sign.
+template <typename T, bool INV>
+__host__ __device__ __forceinline__ cpx<T> rot90(cpx<T> a) {
+    return INV ? mk(-a.im, a.re) : mk(a.im, -a.re);
+}
+
+// ------------------------------------------------------------------ small DFTs
+// v[k] <- sum_m v[m] exp(-+ 2 pi i m k / R)   (minus: forward, plus: INV)
+
+template <typename T, bool INV>
+__host__ __device__ __forceinline__ void dft2(cpx<T>* v) {
+    cpx<T> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+}
+
+template <typename T, bool INV>
+__host__ __device__ __forceinline__ void dft3(cpx<T>* v) {
+    const T h = T(0.5), s = T(0.86602540378443864676372317075294);  // sin(2 pi / 3)
+    cpx<T> t = v[1] + v[2];
+    cpx<T> d = v[1] - v[2];
+    cpx<T> m = v[0] - scale(t, h);
+    cpx<T> r = rot90<T, INV>(scale(d, s));  // -+ i s (x1 - x2)
+    v[0] = v[0] + t;
+    v[1] = m + r;
+    v[2] = m - r;
+}
+
+template <typename T, bool INV>
+__host__ __device__ __forceinline__ void dft4(cpx<T>* v) {
+    cpx<T> s02 = v[0] + v[2], d02 = v[0] - v[2];
+    cpx<T> s13 = v[1] + v[3], d13 = rot90<T, INV>(v[1] - v[3]);
+    v[0] = s02 + s13;
+    v[2] = s02 - s13;
+    v[1] = d02 + d13;
+    v[3] = d02 - d13;
+}
+
+template <typename T, bool INV>
+__host__ __device__ __forceinline__ void dft5(cpx<T>* v) {
+    const T c1 = T(0.30901699437494742410229341718282);   // cos(2 pi / 5)
+    const T c2 = T(-0.80901699437494742410229341718282);  // cos(4 pi / 5)
+    const T s1 = T(0.95105651629515357211643933337938);   // sin(2 pi / 5)
+    const T s2 = T(0.58778525229247312916870595463907);   // sin(4 pi / 5)
+    cpx<T> a1 = v[1] + v[4], b1 = v[1] - v[4];
+    cpx<T> a2 = v[2] + v[3], b2 = v[2] - v[3];
+    cpx<T> x0 = v[0];
+    cpx<T> p1 = x0 + scale(a1, c1) + scale(a2, c2);
+    cpx<T> p2 = x0 + scale(a1, c2) + scale(a2, c1);
+    cpx<T> q1 = rot90<T, INV>(scale(b1, s1) + scale(b2, s2));  // -+ i (s1 b1 + s2 b2)
+    cpx<T> q2 = rot90<T, INV>(scale(b1, s2) - scale(b2, s1));  // -+ i (s2 b1 - s1 b2)
+    v[0] = x0 + a1 + a2;
+    v[1] = p1 + q1;
+    v[4] = p1 - q1;
+    v[2] = p2 + q2;
+    v[3] = p2 - q2;
+}
+
+template <typename T, bool INV>
+__host__ __device__ __forceinline__ void dft8(cpx<T>* v) {
+    const T r = T(0.70710678118654752440084436210485);
+    cpx<T> e[4] = {v[0], v[2], v[4], v[6]};
+    cpx<T> o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<T, INV>(e);
+    dft4<T, INV>(o);
+    // w8^k = exp(-+ 2 pi i k / 8), k = 1, 2, 3
+    cpx<T> o1 = INV ? mk(r * (o[1].re - o[1].im), r * (o[1].re + o[1].im))
+                    : mk(r * (o[1].re + o[1].im), r * (o[1].im - o[1].re));
+    cpx<T> o2 = rot90<T, INV>(o[2]);
+    cpx<T> o3 = INV ? mk(-r * (o[3].re + o[3].im), r * (o[3].re - o[3].im))
+                    : mk(r * (o[3].im - o[3].re), -r * (o[3].re + o[3].im));
+    v[0] = e[0] + o[0];
+    v[4] = e[0] - o[0];
+    v[1] = e[1] + o1;
+    v[5] = e[1] - o1;
+    v[2] = e[2] + o2;
+    v[6] = e[2] - o2;
+    v[3] = e[3] + o3;
+    v[7] = e[3] - o3;
+}
+
+template <typename T, bool INV>
+__host__ __device__ __forceinline__ void dft16(cpx<T>* v) {
+    // cos / sin of pi k / 8, k = 0..7
+    const T C[8] = {T(1.0),
+                    T(0.92387953251128675612818318939679),
+                    T(0.70710678118654752440084436210485),
+                    T(0.38268343236508977172845998403040),
+                    T(0.0),
+                    T(-0.38268343236508977172845998403040),
+                    T(-0.70710678118654752440084436210485),
+                    T(-0.92387953251128675612818318939679)};
+    const T S[8] = {T(0.0),
+                    T(0.38268343236508977172845998403040),
+                    T(0.70710678118654752440084436210485),
+                    T(0.92387953251128675612818318939679),
+                    T(1.0),
+                    T(0.92387953251128675612818318939679),
+                    T(0.70710678118654752440084436210485),
+                    T(0.38268343236508977172845998403040)};
+    cpx<T> e[8], o[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        e[m] = v[2 * m];
+        o[m] = v[2 * m + 1];
+    }
+    dft8<T, INV>(e);
+    dft8<T, INV>(o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cpx<T> w = mk(C[k], INV ? S[k] : -S[k]);
+        cpx<T> t = (k == 0) ? o[k] : o[k] * w;
+        v[k] = e[k] + t;
+        v[k + 8] = e[k] - t;
+    }
+}
+
+template <typename T, int R, bool INV>
+__host__ __device__ __forceinline__ void dft(cpx<T>* v) {
+    if constexpr (R == 2) dft2<T, INV>(v);
+    if constexpr (R == 3) dft3<T, INV>(v);
+    if constexpr (R == 4) dft4<T, INV>(v);
+    if constexpr (R == 5) dft5<T, INV>(v);
+    if constexpr (R == 8) dft8<T, INV>(v);
+    if constexpr (R == 16) dft16<T, INV>(v);
+}
+
+// ------------------------------------------------------------------ radix plans
+constexpr int kMaxStages = 14;
+
+struct RadixPlan {
+    int n;                  // line length
+    int nst;                // number of stages
+    int r[kMaxStages];      // radix of each stage (2, 3, 4, 5, 8 or 16)
+};
+
+// ------------------------------------------------------------------ accessors
+// Column `col` of a tile, element n of the line.
+template <typename T>
+struct SmemTile {
+    cpx<T>* p;
+    int ld;
+    __device__ __forceinline__ cpx<T> ld_(int col, int n) const { return p[n * ld + col]; }
+    __device__ __forceinline__ void st_(int col, int n, cpx<T> v) const { p[n * ld + col] = v; }
+};
+
+template <typename T>
+struct GlobalTile {
+    cpx<T>* p;
+    long long sn;  // element stride along the line
+    __device__ __forceinline__ cpx<T> ld_(int col, int n) const { return p[(long long)n * sn + col]; }
+    __device__ __forceinline__ void st_(int col, int n, cpx<T> v) const { p[(long long)n * sn + col] = v; }
+};
+
+// One Stockham stage over a tile.  tw[e * tws] = exp(-2 pi i e / N) for the
+// line length N (tws > 1 when the table belongs to a longer line).
+template <typename T, int R, bool INV, class Src, class Dst>
+__device__ __forceinline__ void stage(const Src& src, const Dst& dst, int N, int Ns, int ncol,
+                                      const cpx<T>* __restrict__ tw, int tws) {
+    const int nb = N / R;
+    const int total = nb * ncol;
+    const int tstep = N / (Ns * R);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int col = t % ncol;
+        const int j = t / ncol;
+        cpx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src.ld_(col, j + r * nb);
+        const int k = j % Ns;
+        if (Ns > 1) {
+            const int base = k * tstep;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                cpx<T> w = tw[(base * r) * tws];
+                if (INV) w = conjg(w);
+                v[r] = v[r] * w;
+            }
+        }
+        dft<T, R, INV>(v);
+        const int o = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst.st_(col, o + r * Ns, v[r]);
+    }
+}
+
+template <typename T, bool INV, class Src, class Dst>
+__device__ __forceinline__ void stage_any(int R, const Src& src, const Dst& dst, int N, int Ns, int ncol,
+                                          const cpx<T>* __restrict__ tw, int tws) {
+    switch (R) {
+        case 2: stage<T, 2, INV>(src, dst, N, Ns, ncol, tw, tws); break;
+        case 3: stage<T, 3, INV>(src, dst, N, Ns, ncol, tw, tws); break;
+        case 4: stage<T, 4, INV>(src, dst, N, Ns, ncol, tw, tws); break;
+        case 5: stage<T, 5, INV>(src, dst, N, Ns, ncol, tw, tws); break;
+        case 8: stage<T, 8, INV>(src, dst, N, Ns, ncol, tw, tws); break;
+        case 16: stage<T, 16, INV>(src, dst, N, Ns, ncol, tw, tws); break;
+        default: break;
+    }
+}
+
+// Full transform of a tile, src -> dst, through two shared-memory ping-pong
+// buffers A and B (each N x ld).  Stage 0 writes A, so a source that lives in
+// shared memory must be B (or a third buffer), never A.  With a single stage
+// src and dst must not overlap (stage 0 reads and writes in one sweep).
+template <typename T, bool INV, class Src, class Dst>
+__device__ void run_fft(const RadixPlan& rp, const Src& src, const Dst& dst, cpx<T>* A, cpx<T>* B, int ld, int ncol,
+                        const cpx<T>* __restrict__ tw, int tws) {
+    const int N = rp.n;
+    if (rp.nst == 1) {
+        stage_any<T, INV>(rp.r[0], src, dst, N, 1, ncol, tw, tws);
+        return;
+    }
+    SmemTile<T> bufs[2] = {{A, ld}, {B, ld}};
+    int Ns = 1;
+    stage_any<T, INV>(rp.r[0], src, bufs[0], N, Ns, ncol, tw, tws);
+    Ns *= rp.r[0];
+    __syncthreads();
+    int cur = 0;
+    for (int s = 1; s < rp.nst - 1; ++s) {
+        stage_any<T, INV>(rp.r[s], bufs[cur], bufs[cur ^ 1], N, Ns, ncol, tw, tws);
+        Ns *= rp.r[s];
+        cur ^= 1;
+        __syncthreads();
+    }
+    stage_any<T, INV>(rp.r[rp.nst - 1], bufs[cur], dst, N, Ns, ncol, tw, tws);
+}
+
+// Transform from `src` into shared memory.  The result lands in A or B; the
+// returned pointer says which.  Stage 0 writes A, so a shared-memory source
+// must be B.  Ends with __syncthreads().
+template <typename T, bool INV, class Src>
+__device__ cpx<T>* run_fft_to_smem(const RadixPlan& rp, const Src& src, cpx<T>* A, cpx<T>* B, int ld, int ncol,
+                                   const cpx<T>* __restrict__ tw, int tws) {
+    const int N = rp.n;
+    SmemTile<T> bufs[2] = {{A, ld}, {B, ld}};
+    int Ns = 1;
+    stage_any<T, INV>(rp.r[0], src, bufs[0], N, Ns, ncol, tw, tws);
+    Ns *= rp.r[0];
+    __syncthreads();
+    int cur = 0;
+    for (int s = 1; s < rp.nst; ++s) {
+        stage_any<T, INV>(rp.r[s], bufs[cur], bufs[cur ^ 1], N, Ns, ncol, tw, tws);
+        Ns *= rp.r[s];
+        cur ^= 1;
+        __syncthreads();
+    }
+    return bufs[cur].p;
+}
+
+}  // namespace hartree

@@ -1,0 +1,178 @@
+"""Thin PyTorch-facing wrapper over the C ABI: device memory and streams only.
+
+Every computation happens in libhartree_gb300.so; this module allocates
+output tensors, checks dtypes/devices/shapes and passes raw pointers and the
+current CUDA stream to the library.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import capi
+
+_PREC = {"fp64": capi.HARTREE_FP64, "fp32": capi.HARTREE_FP32, "bf16split": capi.HARTREE_FP32_TC_SPLIT}
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(device) -> int:
+    torch = _torch()
+    return int(torch.cuda.current_stream(device).cuda_stream)
+
+
+def atoms_reorder(pos: np.ndarray, n_leaves: int, w: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray]:
+    """Modified recursive bisection (host, FP64): (perm[n], leaf_start[n_leaves + 1])."""
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    n = pos.shape[0]
+    perm = np.empty(max(n, 1), dtype=np.int32)
+    ls = np.empty(int(n_leaves) + 1, dtype=np.int32)
+    wp = None
+    if w is not None:
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
+        wp = w.ctypes.data
+    capi.check(capi.hartree_atoms_reorder(pos.ctypes.data, wp, n, int(n_leaves), perm.ctypes.data, ls.ctypes.data))
+    return perm[:n].copy(), ls
+
+
+class HartreePlan:
+    """One grid / cell / width / precision; owns the library plan and its workspace."""
+
+    def __init__(
+        self,
+        n: Sequence[int],
+        cell: Sequence[float],
+        sigma: float,
+        precision: str = "fp32",
+        cutoff_sigmas: float = 0.0,
+        atoms_per_leaf: int = 0,
+        max_atoms: int = 0,
+        device=None,
+    ):
+        torch = _torch()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+        self.n = tuple(int(v) for v in n)
+        self.cell = tuple(float(v) for v in cell)
+        self.sigma = float(sigma)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        d = capi.hartree_desc()
+        for i in range(3):
+            d.n[i] = self.n[i]
+            d.cell[i] = self.cell[i]
+        d.sigma = self.sigma
+        d.cutoff_sigmas = float(cutoff_sigmas)
+        d.precision = _PREC[precision]
+        d.atoms_per_leaf = int(atoms_per_leaf)
+        d.max_atoms = int(max_atoms)
+        d.flags = 0
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            capi.check(capi.hartree_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+
+    # ------------------------------------------------------------ helpers
+    @property
+    def handle(self) -> int:
+        if self._h is None:
+            raise RuntimeError("plan is closed")
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            capi.hartree_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(capi.hartree_plan_workspace_bytes(self.handle))
+
+    def _grid(self, t, name):
+        torch = _torch()
+        if t is None:
+            return torch.empty(self.n, dtype=self.dtype, device=self.device)
+        if t.dtype != self.dtype or t.device != self.device or tuple(t.shape) != self.n or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous {self.dtype} tensor of shape {self.n} on {self.device}")
+        return t
+
+    def _atoms(self, pos, q):
+        torch = _torch()
+        if pos.dtype != torch.float64 or q.dtype != torch.float64:
+            raise ValueError("pos and q must be float64")
+        if pos.device != self.device or q.device != self.device:
+            raise ValueError("pos and q must live on the plan's device")
+        pos = pos.contiguous().reshape(-1, 3)
+        q = q.contiguous().reshape(-1)
+        if pos.shape[0] != q.shape[0]:
+            raise ValueError("pos and q disagree on the atom count")
+        return pos, q, int(q.shape[0])
+
+    # ------------------------------------------------------------ entry points
+    def splat(self, pos, q, rho=None):
+        pos, q, n = self._atoms(pos, q)
+        rho = self._grid(rho, "rho")
+        capi.check(capi.hartree_splat(self.handle, pos.data_ptr(), q.data_ptr(), n, rho.data_ptr(),
+                                      _stream_handle(self.device)))
+        return rho
+
+    def solve_density(self, rho, vh=None, eh=None):
+        torch = _torch()
+        rho = self._grid(rho, "rho")
+        vh = self._grid(vh, "vh")
+        if eh is None:
+            eh = torch.empty((), dtype=torch.float64, device=self.device)
+        capi.check(capi.hartree_solve_density(self.handle, rho.data_ptr(), vh.data_ptr(), eh.data_ptr(),
+                                              _stream_handle(self.device)))
+        return vh, eh
+
+    def solve(self, pos, q, vh=None, rho=None, eh=None, want_rho: bool = False):
+        torch = _torch()
+        pos, q, n = self._atoms(pos, q)
+        vh = self._grid(vh, "vh")
+        if want_rho and rho is None:
+            rho = self._grid(None, "rho")
+        elif rho is not None:
+            rho = self._grid(rho, "rho")
+        if eh is None:
+            eh = torch.empty((), dtype=torch.float64, device=self.device)
+        capi.check(capi.hartree_solve(self.handle, pos.data_ptr(), q.data_ptr(), n,
+                                      rho.data_ptr() if rho is not None else None, vh.data_ptr(), eh.data_ptr(),
+                                      _stream_handle(self.device)))
+        return (vh, eh, rho) if want_rho else (vh, eh)
+
+    def forces(self, pos, q, vh=None, f=None, phi=None, want_phi: bool = True):
+        torch = _torch()
+        pos, q, n = self._atoms(pos, q)
+        if vh is not None:
+            vh = self._grid(vh, "vh")
+        if f is None:
+            f = torch.empty((n, 3), dtype=torch.float64, device=self.device)
+        if want_phi and phi is None:
+            phi = torch.empty((n,), dtype=torch.float64, device=self.device)
+        capi.check(capi.hartree_forces(self.handle, pos.data_ptr(), q.data_ptr(), n,
+                                       vh.data_ptr() if vh is not None else None, f.data_ptr(),
+                                       phi.data_ptr() if want_phi else None, _stream_handle(self.device)))
+        return (f, phi) if want_phi else f
+
+    def step_host(self, pos: np.ndarray, q: np.ndarray, forces: bool = True):
+        """Host arrays in, (E_H, F or None) out; copies and waits inside the library."""
+        pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
+        n = q.size
+        eh = np.zeros(1, dtype=np.float64)
+        f = np.empty((n, 3), dtype=np.float64) if forces else None
+        capi.check(capi.hartree_step_host(self.handle, pos.ctypes.data, q.ctypes.data, n, eh.ctypes.data,
+                                          f.ctypes.data if forces else None, _stream_handle(self.device)))
+        return float(eh[0]), f

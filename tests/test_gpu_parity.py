@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated per result):
+  FP64 path: V_H relative L2 <= 1e-12, E_H relative <= 1e-12, forces <= 1e-10 Ha/Bohr
+  FP32 path: V_H relative L2 <= 2e-6,  E_H relative <= 1e-7,  forces <= 1e-5 Ha/Bohr
+"""
+import functools
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1209_4506_gb300 import synth
+from paper_1209_4506_gb300.hartree import HartreePlan, atoms_reorder
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {
+    "fp64": dict(v=1e-12, e=1e-12, f=1e-10),
+    "fp32": dict(v=2e-6, e=1e-7, f=1e-5),
+}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), device="cuda")
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_cfg(name):
+    O.set_threads(os.cpu_count() or 1)
+    S = {"cfg1": synth.config1, "cfg2": synth.config2, "cfg5": synth.config5}[name]()
+    return S, O.solve_system(S)
+
+
+def gpu_step(S, precision, pos=None, q=None, order=None, **plan_kw):
+    pos = S.pos if pos is None else pos
+    q = S.q if q is None else q
+    plan = HartreePlan(S.n, S.cell, S.sigma, precision, **plan_kw)
+    if order is not None:
+        pos, q = pos[order], q[order]
+    P, Q = dev(pos), dev(q)
+    vh, eh, rho = plan.solve(P, Q, want_rho=True)
+    f, phi = plan.forces(P, Q, vh)
+    torch.cuda.synchronize()
+    out = dict(vh=vh.cpu().numpy().astype(np.float64), rho=rho.cpu().numpy().astype(np.float64), eh=float(eh.item()),
+               forces=f.cpu().numpy(), phi=phi.cpu().numpy())
+    if order is not None:
+        inv = np.empty_like(order)
+        inv[order] = np.arange(len(order))
+        out["forces"] = out["forces"][inv]
+        out["phi"] = out["phi"][inv]
+    plan.close()
+    return out
+
+
+# ------------------------------------------------------------------ Poisson solve of a given density
+POISSON_SHAPES = [
+    ((24, 30, 36), (5.0, 6.2, 7.4)),
+    ((48, 40, 60), (9.1, 7.7, 11.3)),
+    ((45, 27, 20), (8.0, 5.0, 4.0)),  # odd N1, N2 (radix 3, 5 only)
+    ((16, 16, 16), (4.0, 4.0, 4.0)),
+    ((2, 2, 4), (1.0, 1.5, 2.0)),  # smallest grid: single-stage transforms on every axis
+    ((128, 96, 80), (20.0, 15.0, 12.5)),
+    ((64, 64, 512), (8.0, 8.0, 60.0)),  # long c lines
+    ((512, 8, 8), (60.0, 2.0, 2.0)),  # long a lines
+    ((4096, 4, 4), (400.0, 1.0, 1.0)),  # largest axis, a
+    ((4, 4096, 4), (1.0, 400.0, 1.0)),  # largest axis, b
+    ((4, 4, 4096), (1.0, 1.0, 400.0)),  # largest axis, c
+    ((120, 120, 120), (13.48, 13.48, 13.48)),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,cell", POISSON_SHAPES)
+def test_poisson_matches_oracle(shape, cell, precision):
+    rng = np.random.default_rng(sum(shape))
+    rho = rng.standard_normal(shape)
+    v_ref, e_ref, e_spec, _ = O.poisson(cell, rho)
+    plan = HartreePlan(shape, cell, 0.5, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    r = torch.tensor(rho, dtype=dt, device="cuda")
+    vh, eh = plan.solve_density(r)
+    torch.cuda.synchronize()
+    v = vh.double().cpu().numpy()
+    # the FP32 input is itself rounded: compare against the oracle on the same rounded input
+    if precision == "fp32":
+        v_ref, e_ref, _, _ = O.poisson(cell, rho.astype(np.float32).astype(np.float64))
+    assert rel_l2(v, v_ref) <= TOL[precision]["v"]
+    assert abs(eh.item() - e_ref) <= TOL[precision]["e"] * abs(e_ref)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_poisson_aliasing_rho_and_vh(precision):
+    shape, cell = (24, 30, 36), (5.0, 6.2, 7.4)
+    rng = np.random.default_rng(1)
+    rho = rng.standard_normal(shape)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    rho_in = rho if precision == "fp64" else rho.astype(np.float32).astype(np.float64)
+    v_ref = O.poisson(cell, rho_in)[0]
+    plan = HartreePlan(shape, cell, 0.5, precision)
+    buf = torch.tensor(rho, dtype=dt, device="cuda")
+    plan.solve_density(buf, vh=buf)
+    torch.cuda.synchronize()
+    assert rel_l2(buf.double().cpu().numpy(), v_ref) <= TOL[precision]["v"]
+
+
+# ------------------------------------------------------------------ full step: splat + solve + forces
+@pytest.mark.parametrize("name,precision", [("cfg1", "fp64"), ("cfg2", "fp32"), ("cfg2", "fp64"), ("cfg1", "fp32")])
+def test_full_step_matches_oracle(name, precision):
+    S, ref = oracle_cfg(name)
+    g = gpu_step(S, precision)
+    tol = TOL[precision]
+    assert rel_l2(g["rho"], ref["rho"]) <= tol["v"]
+    assert rel_l2(g["vh"], ref["vh"]) <= tol["v"]
+    assert abs(g["eh"] - ref["eh"]) <= tol["e"] * abs(ref["eh"])
+    assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
+    assert np.max(np.abs(g["phi"] - ref["phi"])) <= tol["f"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_bisection_order_changes_nothing(precision):
+    S, ref = oracle_cfg("cfg2")
+    perm, _ = atoms_reorder(S.pos, 4)
+    a = gpu_step(S, precision)
+    b = gpu_step(S, precision, order=perm)
+    rnd = np.random.default_rng(0).permutation(S.n_atoms)
+    c = gpu_step(S, precision, order=rnd)
+    tol = TOL[precision]
+    for other in (b, c):
+        assert rel_l2(other["vh"], a["vh"]) <= tol["v"]
+        assert np.max(np.abs(other["forces"] - a["forces"])) <= tol["f"]
+    assert rel_l2(b["vh"], ref["vh"]) <= tol["v"]
+
+
+def test_forces_central_differences_fp64_gpu():
+    """F = -dE/dR on the GPU FP64 path itself, all 64 atoms of the 2x2x2 cell, h = 1e-4."""
+    S = synth.config2()
+    plan = HartreePlan(S.n, S.cell, S.sigma, "fp64")
+    P, Q = dev(S.pos), dev(S.q)
+    vh, eh = plan.solve(P, Q)
+    f, _ = plan.forces(P, Q, vh)
+    F = f.cpu().numpy()
+    h = 1e-4
+    # all 6 displaced copies of every atom, energies only
+    E = np.empty((S.n_atoms, 3, 2))
+    for i in range(S.n_atoms):
+        for d in range(3):
+            for s, sign in enumerate((+1.0, -1.0)):
+                p = S.pos.copy()
+                p[i, d] += sign * h
+                _, e = plan.solve(dev(p), Q, vh=vh)
+                E[i, d, s] = e.item()
+    fd = -(E[:, :, 0] - E[:, :, 1]) / (2 * h)
+    assert np.max(np.abs(fd - F)) <= 1e-7
+    plan.close()
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_edge_no_atoms(precision):
+    S = synth.config1()
+    plan = HartreePlan(S.n, S.cell, S.sigma, precision)
+    P = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    Q = torch.empty((0,), dtype=torch.float64, device="cuda")
+    vh, eh, rho = plan.solve(P, Q, want_rho=True)
+    f, phi = plan.forces(P, Q, vh)
+    torch.cuda.synchronize()
+    assert float(rho.abs().max()) == 0.0 and float(vh.abs().max()) == 0.0 and eh.item() == 0.0
+    assert f.numel() == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_edge_single_charged_atom_unwrapped_positions(precision):
+    """A net charge (G = 0 dropped) and positions far outside [0, L)."""
+    cell = (7.0, 8.0, 9.0)
+    n = (36, 40, 48)
+    pos = np.array([[-13.3, 25.1, 4.4], [3.0, -0.2, 100.7]])
+    q = np.array([0.8, 0.0])
+    S = synth.System("edge", n, cell, 0.7, pos, q, precision)
+    ref = O.solve_system(S)
+    g = gpu_step(S, precision)
+    tol = TOL[precision]
+    assert rel_l2(g["vh"], ref["vh"]) <= tol["v"]
+    assert abs(g["eh"] - ref["eh"]) <= tol["e"] * abs(ref["eh"])
+    assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_edge_wide_cutoff_many_images(precision):
+    """Cutoff box wider than the cell: one grid point receives several images."""
+    S = synth.random_system((20, 24, 30), (3.0, 3.5, 4.0), 5, 0.6, seed=77, precision=precision)
+    ref = O.solve_system(S)
+    g = gpu_step(S, precision, cutoff_sigmas=8.0)
+    tol = TOL[precision]
+    assert rel_l2(g["vh"], ref["vh"]) <= tol["v"]
+    assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
+
+
+def test_forces_recompute_when_vh_is_null():
+    S, ref = oracle_cfg("cfg2")
+    plan = HartreePlan(S.n, S.cell, S.sigma, "fp32")
+    f, phi = plan.forces(dev(S.pos), dev(S.q), vh=None)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(f.cpu().numpy() - ref["forces"])) <= TOL["fp32"]["f"]
+
+
+def test_step_host_end_to_end():
+    S, ref = oracle_cfg("cfg2")
+    plan = HartreePlan(S.n, S.cell, S.sigma, "fp32")
+    eh, f = plan.step_host(S.pos, S.q)
+    assert abs(eh - ref["eh"]) <= TOL["fp32"]["e"] * abs(ref["eh"])
+    assert np.max(np.abs(f - ref["forces"])) <= TOL["fp32"]["f"]
+
+
+def test_too_many_atoms_is_rejected():
+    from paper_1209_4506_gb300 import capi
+
+    S = synth.config1()
+    plan = HartreePlan(S.n, S.cell, S.sigma, "fp64", max_atoms=4)
+    with pytest.raises(capi.HartreeError) as ei:
+        plan.solve(dev(S.pos), dev(S.q))
+    assert ei.value.status == capi.HARTREE_ERR_INVALID
+
+
+def test_repeat_runs_are_bitwise_deterministic():
+    S = synth.config2()
+    a = gpu_step(S, "fp32")
+    b = gpu_step(S, "fp32")
+    assert np.array_equal(a["vh"], b["vh"]) and a["eh"] == b["eh"] and np.array_equal(a["forces"], b["forces"])
