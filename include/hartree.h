@@ -68,7 +68,7 @@ typedef struct {
     double cell[3];       /* L1, L2, L3 in Bohr, > 0                                        */
     double sigma;         /* Gaussian width s in Bohr, > 0                                  */
     double cutoff_sigmas; /* per-axis truncation radius in units of s; 0 = default
-                             (8 for FP64, 6 for FP32); must not exceed 16                   */
+                             (8 for FP64, 5 for FP32); must not exceed 16                   */
     int precision;        /* a hartree_precision                                            */
     int atoms_per_leaf;   /* atoms per bisection leaf used by the splat; 0 = default 16     */
     int max_atoms;        /* largest atom count any call on this plan will pass; 0 = 65536 */

@@ -109,9 +109,23 @@ int upload_tables(Plan& p) {
         }
         cudaError_t e = cudaMemcpy(p.tw[d], buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice);
         if (e) return cuda_fail(e, "upload twiddles");
+        std::vector<T> pairs(4 * (size_t)p.n[d]);  // (hi.re, hi.im, lo.re, lo.im) per k
+        for (int k = 0; k < p.n[d]; ++k) {
+            const T hr = (T)re[k], hi = (T)im[k];
+            pairs[4 * k] = hr;
+            pairs[4 * k + 1] = hi;
+            pairs[4 * k + 2] = (T)(re[k] - (double)hr);
+            pairs[4 * k + 3] = (T)(im[k] - (double)hi);
+        }
+        e = cudaMemcpy(p.twp[d], pairs.data(), pairs.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e) return cuda_fail(e, "upload twiddle pairs");
         const int len = d == 2 ? p.nh : p.n[d];
         std::vector<double> g = gsq_table(p.n[d], len, p.L[d]);
-        std::vector<T> gb(g.begin(), g.end());
+        std::vector<T> gb(2 * (size_t)len);  // |G_d|^2 as a high part and the rounding remainder
+        for (int k = 0; k < len; ++k) {
+            gb[2 * k] = (T)g[k];
+            gb[2 * k + 1] = (T)(g[k] - (double)gb[2 * k]);
+        }
         e = cudaMemcpy(p.gsq[d], gb.data(), gb.size() * sizeof(T), cudaMemcpyHostToDevice);
         if (e) return cuda_fail(e, "upload |G|^2 tables");
     }
@@ -119,8 +133,9 @@ int upload_tables(Plan& p) {
 }
 
 void free_plan(Plan& p) {
-    void* ptrs[] = {p.W, p.R, p.tw[0], p.tw[1], p.tw[2], p.gsq[0], p.gsq[1], p.gsq[2], p.eh_partials,
-                    p.leaf_box, p.force_partials, p.d_pos, p.d_q, p.d_f, p.d_eh};
+    void* ptrs[] = {p.W,           p.R,        p.tw[0],         p.tw[1], p.tw[2], p.twp[0], p.twp[1], p.twp[2], p.gsq[0],
+                    p.gsq[1],      p.gsq[2],   p.eh_partials,   p.leaf_box,
+                    p.atom_prep,   p.atom_fac, p.atom_dfac, p.force_partials, p.d_pos,   p.d_q,   p.d_f,   p.d_eh};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -187,7 +202,7 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         p.ldc = (p.nh + align - 1) / align * align;
     }
     p.sigma = d.sigma;
-    p.rc = (d.cutoff_sigmas > 0.0 ? d.cutoff_sigmas : (p.prec == HARTREE_FP64 ? 8.0 : 6.0)) * d.sigma;
+    p.rc = (d.cutoff_sigmas > 0.0 ? d.cutoff_sigmas : (p.prec == HARTREE_FP64 ? 8.0 : 5.0)) * d.sigma;
     p.omega = p.L[0] * p.L[1] * p.L[2];
     p.dV = p.omega / ((double)p.n[0] * p.n[1] * p.n[2]);
     p.apl = d.atoms_per_leaf > 0 ? d.atoms_per_leaf : 16;
@@ -224,8 +239,8 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
     p.smem_c = 2 * (size_t)(p.M + 1) * (p.c_lines + 1) * cs;
     p.smem_b = 2 * (size_t)p.n[1] * p.b_cols * cs;
     p.smem_a = 2 * (size_t)p.n[0] * p.a_cols * cs;
-    const int a_chunks = (p.nh + p.a_cols - 1) / p.a_cols;
-    p.n_eh_partials = p.n[1] * a_chunks;
+    p.n_eh_partials = p.n[1] * p.nh;  // enough for one a-pass CTA per (b, column)
+    p.use_fast = fast_pass_mask(p);
     p.max_force_slabs = 1216;
 
     const size_t ntot = (size_t)p.n[0] * p.n[1] * p.n[2];
@@ -238,11 +253,17 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         {&p.tw[0], (size_t)p.n[0] * cs},
         {&p.tw[1], (size_t)p.n[1] * cs},
         {&p.tw[2], (size_t)p.n[2] * cs},
-        {&p.gsq[0], (size_t)p.n[0] * p.real_size},
-        {&p.gsq[1], (size_t)p.n[1] * p.real_size},
-        {&p.gsq[2], (size_t)p.nh * p.real_size},
+        {&p.twp[0], (size_t)p.n[0] * 2 * cs},
+        {&p.twp[1], (size_t)p.n[1] * 2 * cs},
+        {&p.twp[2], (size_t)p.n[2] * 2 * cs},
+        {&p.gsq[0], (size_t)p.n[0] * cs},
+        {&p.gsq[1], (size_t)p.n[1] * cs},
+        {&p.gsq[2], (size_t)p.nh * cs},
         {(void**)&p.eh_partials, (size_t)p.n_eh_partials * sizeof(double)},
-        {(void**)&p.leaf_box, (size_t)p.max_leaves * 6 * sizeof(double)},
+        {(void**)&p.leaf_box, (size_t)p.max_leaves * 6 * sizeof(int)},
+        {&p.atom_prep, (size_t)p.max_atoms * sizeof(AtomPrep<double>)},
+        {&p.atom_fac, (size_t)p.max_atoms * 3 * p.box_max * p.real_size},
+        {&p.atom_dfac, (size_t)p.max_atoms * 3 * p.box_max * p.real_size},
         {(void**)&p.force_partials, (size_t)(p.max_atoms + p.max_force_slabs) * 4 * sizeof(double)},
         {(void**)&p.d_pos, (size_t)p.max_atoms * 3 * sizeof(double)},
         {(void**)&p.d_q, (size_t)p.max_atoms * sizeof(double)},
@@ -263,6 +284,7 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
     int st = p.prec == HARTREE_FP64 ? upload_tables<double>(p) : upload_tables<float>(p);
     if (st == HARTREE_OK) {
         cudaError_t e = configure_poisson_kernels(p);
+        if (e == cudaSuccess) e = configure_fast_kernels(p);
         if (e == cudaSuccess) e = configure_atom_kernels(p);
         if (e != cudaSuccess) st = cuda_fail(e, "plan_create: kernel attributes");
     }
@@ -311,7 +333,7 @@ int hartree_solve(hartree_plan plan, const double* pos, const double* q, int n, 
 
 int hartree_forces(hartree_plan plan, const double* pos, const double* q, int n, const void* vh, double* f,
                    double* phi, void* stream) {
-    if (!plan || !f || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "forces: null argument");
+    if (!plan || (n > 0 && (!pos || !q || !f))) return fail(HARTREE_ERR_INVALID, "forces: null argument");
     if (n < 0 || n > plan->p.max_atoms)
         return fail(HARTREE_ERR_INVALID, "forces: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
     cudaStream_t s = (cudaStream_t)stream;

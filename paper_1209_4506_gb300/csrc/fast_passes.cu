@@ -1,0 +1,435 @@
+// fast_passes.cu -- compile-time specialised Poisson passes for line lengths
+// 16 .. 1024 that are powers of two (the cubic 32^3, 256^3 and 512^3 grids).
+//
+// Same five-pass schedule as poisson.cu (Sec. 2.1 / Sec. 3.2.4: c, b, a with
+// the Green multiply and E_H, b^-1, c^-1), but every radix, stage stride and
+// thread->butterfly map is a compile-time constant:
+//   * each thread owns BPT butterflies per stage and keeps them in registers;
+//     a stage reads all of them, waits once, and writes them back in place,
+//     so one shared-memory tile (no ping-pong) holds the lines;
+//   * the first stage reads HBM directly and the last stage writes HBM
+//     directly (coalesced: columns for the b/a passes, lines for the c passes);
+//   * twiddles live in shared memory as FP32 high/low pairs, and butterfly
+//     constants are split the same way, so FP32 rounding carries no
+//     systematic magnitude bias into E_H.
+#include "internal.cuh"
+
+namespace hartree {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ cpx<T> twmul(cpx<T> a, const TwPair<T>& w, bool inv) {
+    const T hi_im = inv ? -w.h.im : w.h.im;
+    const T lo_im = inv ? -w.l.im : w.l.im;
+    if constexpr (sizeof(T) == 4) {
+        const float tr = a.re * w.l.re - a.im * lo_im;
+        const float ti = a.re * lo_im + a.im * w.l.re;
+        return mk(fmaf(a.re, w.h.re, fmaf(-a.im, hi_im, tr)), fmaf(a.re, hi_im, fmaf(a.im, w.h.re, ti)));
+    } else {
+        return mk(a.re * w.h.re - a.im * hi_im, a.re * hi_im + a.im * w.h.re);
+    }
+}
+
+template <int R0, int R1, int R2>
+struct RP {
+    static constexpr int N = R0 * R1 * R2;
+    static constexpr int NST = R2 == 1 ? 2 : 3;
+};
+
+// ------------------------------------------------------------------ accessors
+template <typename T, int COLS>
+struct ColSmem {  // [n][COLS]
+    cpx<T>* p;
+    __device__ __forceinline__ cpx<T> ld_(int col, int n) const { return p[n * COLS + col]; }
+    __device__ __forceinline__ void st_(int col, int n, cpx<T> v) const { p[n * COLS + col] = v; }
+};
+
+template <typename T>
+struct ColGlobal {  // column `col` of a strided tile; inactive columns read 0 and store nothing
+    cpx<T>* p;
+    long long sn;
+    int nc;
+    __device__ __forceinline__ cpx<T> ld_(int col, int n) const {
+        return col < nc ? p[(long long)n * sn + col] : mk(T(0), T(0));
+    }
+    __device__ __forceinline__ void st_(int col, int n, cpx<T> v) const {
+        if (col < nc) p[(long long)n * sn + col] = v;
+    }
+};
+
+__device__ __forceinline__ int pidx(int n) { return n + (n >> 4); }  // one pad slot per 16 elements
+
+template <typename T>
+struct LineSmem {  // one line, padded
+    cpx<T>* p;
+    __device__ __forceinline__ cpx<T> ld_(int, int n) const { return p[pidx(n)]; }
+    __device__ __forceinline__ void st_(int, int n, cpx<T> v) const { p[pidx(n)] = v; }
+};
+
+template <typename T>
+struct LineRealIn {  // z[n] = rho[2n] + i rho[2n+1]
+    const cpx<T>* z;
+    bool act;
+    __device__ __forceinline__ cpx<T> ld_(int, int n) const { return act ? z[n] : mk(T(0), T(0)); }
+};
+
+template <typename T>
+struct LineRealOut {
+    cpx<T>* z;
+    bool act;
+    __device__ __forceinline__ void st_(int, int n, cpx<T> v) const {
+        if (act) z[n] = v;
+    }
+};
+
+// Z[k] = (X[k] + conj X[M-k]) + i w^-k (X[k] - conj X[M-k]) from the half spectrum (c2r pre-step)
+template <typename T>
+struct LineC2RIn {
+    const cpx<T>* x;
+    const TwPair<T>* tw;  // exp(-2 pi i k / N3)
+    int M;
+    bool act;
+    __device__ __forceinline__ cpx<T> ld_(int, int k) const {
+        if (!act) return mk(T(0), T(0));
+        const cpx<T> x1 = x[k];
+        const cpx<T> x2 = conjg(x[M - k]);
+        const cpx<T> Ep = x1 + x2;
+        const cpx<T> Op = twmul(x1 - x2, tw[k], true);
+        return mk(Ep.re - Op.im, Ep.im + Op.re);
+    }
+};
+
+struct NoPost {
+    template <typename T>
+    __device__ __forceinline__ void operator()(int, int, cpx<T>&) const {}
+};
+
+// One Stockham stage (radix R, sub-transform NS) for the BPT butterflies
+// j = j0 + t JSTEP of this thread; SYNC when src and dst share storage.
+template <typename T, int N, int R, int NS, int BPT, int JSTEP, int TWS, bool INV, bool SYNC, class Src, class Dst,
+          class Post>
+__device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, int j0, const TwPair<T>* TW,
+                                       const Post& post) {
+    constexpr int NB = N / R;
+    cpx<T> v[BPT][R];
+#pragma unroll
+    for (int t = 0; t < BPT; ++t) {
+        const int j = j0 + t * JSTEP;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[t][r] = src.ld_(col, j + r * NB);
+    }
+    if constexpr (SYNC) __syncthreads();
+#pragma unroll
+    for (int t = 0; t < BPT; ++t) {
+        const int j = j0 + t * JSTEP;
+        const int k = j % NS;
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[t][r] = twmul(v[t][r], TW[(k * r * (N / (NS * R))) * TWS], INV);
+        }
+        dft<T, R, INV>(v[t]);
+        const int o = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            post(col, o + r * NS, v[t][r]);
+            dst.st_(col, o + r * NS, v[t][r]);
+        }
+    }
+}
+
+// Whole transform of a tile: stage 0 from src, the rest in place in `sm`,
+// the last stage through `post` into dst.  Threads: col, j0 in [0, JSTEP).
+template <typename T, int R0, int R1, int R2, int JSTEP, int TWS, bool INV, bool FIRST_SYNC, class Src, class Sm,
+          class Dst, class Post>
+__device__ __forceinline__ void ftransform(const Src& src, const Sm& sm, const Dst& dst, int col, int j0,
+                                           const TwPair<T>* TW, const Post& post) {
+    constexpr int N = R0 * R1 * R2;
+    constexpr int B0 = (N / R0) / JSTEP, B1 = (N / R1) / JSTEP, B2 = (N / R2) / JSTEP;
+    static_assert(B0 * JSTEP * R0 == N && B1 * JSTEP * R1 == N, "butterflies must divide evenly");
+    if constexpr (R2 == 1) {
+        fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{});
+        __syncthreads();
+        fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, dst, col, j0, TW, post);
+    } else {
+        static_assert(B2 * JSTEP * R2 == N, "butterflies must divide evenly");
+        fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{});
+        __syncthreads();
+        fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, sm, col, j0, TW, NoPost{});
+        __syncthreads();
+        fstage<T, N, R2, R0 * R1, B2, JSTEP, TWS, INV, true>(sm, dst, col, j0, TW, post);
+    }
+}
+
+// ------------------------------------------------------------------ b and a passes
+// MODE 0: forward, 1: inverse (b axis);  2: forward, Green, E_H, inverse (a axis)
+// Resident CTAs per SM asked of the register allocator: at least two, so one
+// CTA's loads overlap another's butterflies.
+template <int NT>
+constexpr int min_ctas() {
+    return NT >= 512 ? 2 : (NT >= 256 ? 3 : 4);
+}
+
+template <typename T, int COLS, int NT, int R0, int R1, int R2, int MODE>
+__global__ void __launch_bounds__(NT, min_ctas<NT>()) k_col_fast(FastArgs<T> a) {
+    constexpr int N = R0 * R1 * R2;
+    constexpr int JSTEP = NT / COLS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[NT / 32];
+    cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
+    TwPair<T>* TW = reinterpret_cast<TwPair<T>*>(S + N * COLS);
+    const TwPair<T>* twg = MODE == 2 ? a.twpa : a.twpb;
+    for (int k = threadIdx.x; k < N; k += NT) TW[k] = twg[k];
+    const int chunks = MODE == 2 ? a.a_chunks : a.b_chunks;
+    const int line = blockIdx.x / chunks;
+    const int c0 = (blockIdx.x - line * chunks) * COLS;
+    const int nc = min(COLS, a.nh - c0);
+    ColGlobal<T> g{MODE == 2 ? a.W + (long long)line * a.ldc + c0 : a.W + (long long)line * a.n2 * a.ldc + c0,
+                   MODE == 2 ? (long long)a.n2 * a.ldc : (long long)a.ldc, nc};
+    ColSmem<T, COLS> sm{S};
+    const int col = threadIdx.x % COLS, j0 = threadIdx.x / COLS;
+    __syncthreads();
+    if constexpr (MODE != 2) {
+        ftransform<T, R0, R1, R2, JSTEP, 1, MODE == 1, false>(g, sm, g, col, j0, TW, NoPost{});
+    } else {
+        // forward, then 4 pi / |G|^2 / N and the E_H partial on the last stage's outputs
+        const cpx<T> gb = a.gsqb[line];
+        const int k3 = c0 + col;
+        const cpx<T> gc = a.gsqc[k3 < a.nh ? k3 : 0];
+        const T mult = (k3 == 0 || k3 == a.M) ? T(1) : T(2);
+        T sum = T(0), comp = T(0);
+        auto green = [&](int c, int k1, cpx<T>& v) {
+            const cpx<T> ga = a.gsqa[k1];
+            const T G2 = ((ga.re + gb.re) + gc.re) + ((ga.im + gb.im) + gc.im);
+            const T inv = (G2 > T(0)) ? T(1) / G2 : T(0);
+            if (c < nc) {
+                const T term = mult * (v.re * v.re + v.im * v.im) * inv - comp;
+                const T t = sum + term;
+                comp = (t - sum) - term;
+                sum = t;
+            }
+            v = scale(v, inv * a.green_scale);
+        };
+        ftransform<T, R0, R1, R2, JSTEP, 1, false, false>(g, sm, sm, col, j0, TW, green);
+        const double bs = block_sum_double((double)sum - (double)comp, red);
+        if (threadIdx.x == 0) a.eh_partials[blockIdx.x] = bs;
+        __syncthreads();
+        ftransform<T, R0, R1, R2, JSTEP, 1, true, true>(sm, sm, g, col, j0, TW, NoPost{});
+    }
+}
+
+// ------------------------------------------------------------------ c passes
+template <typename T, int LINES, int NT, int R0, int R1, int R2>
+__global__ void __launch_bounds__(NT, min_ctas<NT>()) k_r2c_fast(const T* __restrict__ rho, FastArgs<T> a) {
+    constexpr int M = R0 * R1 * R2;
+    constexpr int TPL = NT / LINES;
+    constexpr int LDP = M + M / 16 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
+    TwPair<T>* TW = reinterpret_cast<TwPair<T>*>(S + LINES * LDP);
+    for (int k = threadIdx.x; k < 2 * M; k += NT) TW[k] = a.twpc[k];
+    const int l = threadIdx.x / TPL, j0 = threadIdx.x % TPL;
+    const long long gline = (long long)blockIdx.x * LINES + l;
+    const bool act = gline < (long long)a.n1 * a.n2;
+    LineRealIn<T> src{reinterpret_cast<const cpx<T>*>(rho + (act ? gline : 0) * a.n3), act};
+    LineSmem<T> sm{S + l * LDP};
+    __syncthreads();
+    // M-point transform of z (twiddles exp(-2 pi i e / M) = table entry 2e)
+    ftransform<T, R0, R1, R2, TPL, 2, false, false>(src, sm, sm, 0, j0, TW, NoPost{});
+    __syncthreads();
+    // X[k] = E[k] + w^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M
+    if (act) {
+        cpx<T>* out = a.W + gline * a.ldc;
+        const T half = T(0.5);
+        for (int k = j0; k <= M; k += TPL) {
+            const cpx<T> z1 = sm.ld_(0, k == M ? 0 : k);
+            const cpx<T> z2 = conjg(sm.ld_(0, k == 0 ? 0 : M - k));
+            const cpx<T> E = scale(z1 + z2, half);
+            const cpx<T> d = z1 - z2;
+            const cpx<T> O = mk(d.im * half, -d.re * half);
+            out[k] = E + twmul(O, TW[k], false);
+        }
+    }
+}
+
+template <typename T, int LINES, int NT, int R0, int R1, int R2>
+__global__ void __launch_bounds__(NT, min_ctas<NT>()) k_c2r_fast(T* __restrict__ vout, FastArgs<T> a) {
+    constexpr int M = R0 * R1 * R2;
+    constexpr int TPL = NT / LINES;
+    constexpr int LDP = M + M / 16 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
+    TwPair<T>* TW = reinterpret_cast<TwPair<T>*>(S + LINES * LDP);
+    for (int k = threadIdx.x; k < 2 * M; k += NT) TW[k] = a.twpc[k];
+    const int l = threadIdx.x / TPL, j0 = threadIdx.x % TPL;
+    const long long gline = (long long)blockIdx.x * LINES + l;
+    const bool act = gline < (long long)a.n1 * a.n2;
+    const long long gl = act ? gline : 0;
+    LineSmem<T> sm{S + l * LDP};
+    __syncthreads();
+    LineC2RIn<T> src{a.W + gl * a.ldc, TW, M, act};
+    LineRealOut<T> dst{reinterpret_cast<cpx<T>*>(vout + gl * a.n3), act};
+    ftransform<T, R0, R1, R2, TPL, 2, true, false>(src, sm, dst, 0, j0, TW, NoPost{});
+}
+
+// ------------------------------------------------------------------ dispatch
+template <typename T, int COLS, int NT, int R0, int R1, int R2>
+struct ColCfg {
+    static constexpr int cols = COLS, n = R0 * R1 * R2;
+    static size_t smem() { return (size_t)n * COLS * sizeof(cpx<T>) + (size_t)n * sizeof(TwPair<T>); }
+    static cudaError_t configure(int optin) {
+        cudaError_t e;
+        if ((e = allow_max_dynamic_smem(k_col_fast<T, COLS, NT, R0, R1, R2, 0>, optin))) return e;
+        if ((e = allow_max_dynamic_smem(k_col_fast<T, COLS, NT, R0, R1, R2, 1>, optin))) return e;
+        return allow_max_dynamic_smem(k_col_fast<T, COLS, NT, R0, R1, R2, 2>, optin);
+    }
+    static void launch(int mode, unsigned grid, const FastArgs<T>& a, cudaStream_t s) {
+        if (mode == 0) k_col_fast<T, COLS, NT, R0, R1, R2, 0><<<grid, NT, smem(), s>>>(a);
+        if (mode == 1) k_col_fast<T, COLS, NT, R0, R1, R2, 1><<<grid, NT, smem(), s>>>(a);
+        if (mode == 2) k_col_fast<T, COLS, NT, R0, R1, R2, 2><<<grid, NT, smem(), s>>>(a);
+    }
+};
+
+template <typename T, int LINES, int NT, int R0, int R1, int R2>
+struct LineCfg {
+    static constexpr int lines = LINES, m = R0 * R1 * R2;
+    static size_t smem() {
+        return (size_t)LINES * (m + m / 16 + 1) * sizeof(cpx<T>) + (size_t)2 * m * sizeof(TwPair<T>);
+    }
+    static cudaError_t configure(int optin) {
+        cudaError_t e;
+        if ((e = allow_max_dynamic_smem(k_r2c_fast<T, LINES, NT, R0, R1, R2>, optin))) return e;
+        return allow_max_dynamic_smem(k_c2r_fast<T, LINES, NT, R0, R1, R2>, optin);
+    }
+    static void launch(bool inverse, unsigned grid, const void* in, void* out, const FastArgs<T>& a,
+                       cudaStream_t s) {
+        if (!inverse)
+            k_r2c_fast<T, LINES, NT, R0, R1, R2><<<grid, NT, smem(), s>>>(static_cast<const T*>(in), a);
+        else
+            k_c2r_fast<T, LINES, NT, R0, R1, R2><<<grid, NT, smem(), s>>>(static_cast<T*>(out), a);
+    }
+};
+
+// Column-pass configurations by line length (FP32 rows of 16 complex = 128 B; FP64 rows of 8).
+template <typename T, class F>
+bool with_col_cfg(int n, F&& f) {
+    constexpr bool d = sizeof(T) == 8;
+    switch (n) {
+        case 16: f(ColCfg<T, d ? 16 : 32, d ? 64 : 128, 4, 4, 1>{}); return true;
+        case 32: f(ColCfg<T, d ? 16 : 32, d ? 64 : 128, 8, 4, 1>{}); return true;
+        case 64: f(ColCfg<T, d ? 8 : 16, d ? 64 : 128, 8, 8, 1>{}); return true;
+        case 128: f(ColCfg<T, d ? 8 : 16, d ? 64 : 128, 16, 8, 1>{}); return true;
+        case 256: f(ColCfg<T, d ? 8 : 16, d ? 128 : 256, 16, 16, 1>{}); return true;
+        case 512: f(ColCfg<T, d ? 8 : 16, d ? 256 : 512, 8, 8, 8>{}); return true;
+        case 1024: f(ColCfg<T, 8, 512, 16, 8, 8>{}); return true;
+        default: return false;
+    }
+}
+
+// c-pass configurations by M = N3 / 2.
+template <typename T, class F>
+bool with_line_cfg(int m, F&& f) {
+    switch (m) {
+        case 16: f(LineCfg<T, 32, 128, 4, 4, 1>{}); return true;
+        case 32: f(LineCfg<T, 32, 128, 8, 4, 1>{}); return true;
+        case 64: f(LineCfg<T, 16, 128, 8, 8, 1>{}); return true;
+        case 128: f(LineCfg<T, 16, 128, 16, 8, 1>{}); return true;
+        case 256: f(LineCfg<T, 16, 256, 16, 16, 1>{}); return true;
+        case 512: f(LineCfg<T, 4, 256, 8, 8, 8>{}); return true;
+        case 1024: f(LineCfg<T, 4, 256, 16, 8, 8>{}); return true;
+        default: return false;
+    }
+}
+
+template <typename T>
+FastArgs<T> make_fast_args(const Plan& p) {
+    FastArgs<T> a;
+    a.n1 = p.n[0];
+    a.n2 = p.n[1];
+    a.n3 = p.n[2];
+    a.M = p.M;
+    a.nh = p.nh;
+    a.ldc = p.ldc;
+    a.twpa = static_cast<const TwPair<T>*>(p.twp[0]);
+    a.twpb = static_cast<const TwPair<T>*>(p.twp[1]);
+    a.twpc = static_cast<const TwPair<T>*>(p.twp[2]);
+    a.gsqa = static_cast<const cpx<T>*>(p.gsq[0]);
+    a.gsqb = static_cast<const cpx<T>*>(p.gsq[1]);
+    a.gsqc = static_cast<const cpx<T>*>(p.gsq[2]);
+    a.W = static_cast<cpx<T>*>(p.W);
+    a.green_scale = T(4.0 * 3.14159265358979323846 / ((double)p.n[0] * p.n[1] * p.n[2]));
+    a.eh_partials = p.eh_partials;
+    a.a_chunks = 1;
+    a.b_chunks = 1;
+    with_col_cfg<T>(p.n[0], [&](auto c) { a.a_chunks = (p.nh + c.cols - 1) / c.cols; });
+    with_col_cfg<T>(p.n[1], [&](auto c) { a.b_chunks = (p.nh + c.cols - 1) / c.cols; });
+    return a;
+}
+
+}  // namespace
+
+// Which passes have a specialised kernel for this plan (bit 0: c, bit 1: b, bit 2: a).
+template <typename T>
+int fast_pass_mask_t(const Plan& p) {
+    int m = 0;
+    if (with_line_cfg<T>(p.M, [](auto) {})) m |= 1;
+    if (with_col_cfg<T>(p.n[1], [](auto) {})) m |= 2;
+    if (with_col_cfg<T>(p.n[0], [](auto) {})) m |= 4;
+    return m;
+}
+
+int fast_pass_mask(const Plan& p) {
+    return p.prec == HARTREE_FP64 ? fast_pass_mask_t<double>(p) : fast_pass_mask_t<float>(p);
+}
+
+template <typename T>
+cudaError_t configure_fast_t(const Plan& p, int optin) {
+    cudaError_t e = cudaSuccess;
+    auto cfg = [&](auto c) {
+        if (e == cudaSuccess && c.smem() + 2048 > (size_t)optin) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) e = c.configure(optin);
+    };
+    with_line_cfg<T>(p.M, cfg);
+    with_col_cfg<T>(p.n[1], cfg);
+    with_col_cfg<T>(p.n[0], cfg);
+    return e;
+}
+
+cudaError_t configure_fast_kernels(const Plan& p) {
+    int optin = 0;
+    cudaError_t e = optin_smem(&optin);
+    if (e != cudaSuccess) return e;
+    return p.prec == HARTREE_FP64 ? configure_fast_t<double>(p, optin) : configure_fast_t<float>(p, optin);
+}
+
+// pass: 0 = c r2c (rho -> W), 1 = b forward, 2 = a with Green, 3 = b inverse, 4 = c c2r (W -> vh).
+// Returns the number of CTAs launched (the a pass's E_H partial count), or -1 if not specialised.
+template <typename T>
+long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s) {
+    FastArgs<T> a = make_fast_args<T>(p);
+    long long grid = -1;
+    if (pass == 0 || pass == 4) {
+        with_line_cfg<T>(p.M, [&](auto c) {
+            grid = ((long long)p.n[0] * p.n[1] + c.lines - 1) / c.lines;
+            c.launch(pass == 4, (unsigned)grid, rho, vh, a, s);
+        });
+    } else if (pass == 1 || pass == 3) {
+        with_col_cfg<T>(p.n[1], [&](auto c) {
+            grid = (long long)p.n[0] * a.b_chunks;
+            c.launch(pass == 3 ? 1 : 0, (unsigned)grid, a, s);
+        });
+    } else {
+        with_col_cfg<T>(p.n[0], [&](auto c) {
+            grid = (long long)p.n[1] * a.a_chunks;
+            c.launch(2, (unsigned)grid, a, s);
+        });
+    }
+    return grid;
+}
+
+long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s) {
+    return p.prec == HARTREE_FP64 ? launch_fast_pass_t<double>(p, pass, rho, vh, s)
+                                  : launch_fast_pass_t<float>(p, pass, rho, vh, s);
+}
+
+}  // namespace hartree

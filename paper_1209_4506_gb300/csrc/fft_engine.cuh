@@ -55,6 +55,27 @@ __host__ __device__ __forceinline__ cpx<T> rot90(cpx<T> a) {
     return INV ? mk(-a.im, a.re) : mk(a.im, -a.re);
 }
 
+// ------------------------------------------------------------------ constants
+// Multiplication by a real constant c.  In FP32 the product uses c split into
+// a rounded high part and the remainder, so the constant carries no rounding
+// bias: a single-rounded sqrt(1/2) shrinks |w| below 1 at every radix-8
+// stage, which shows up as a systematic loss of spectral energy (E_H).
+template <typename T>
+__host__ __device__ __forceinline__ T kmul(T x, double c) {
+    if constexpr (sizeof(T) == 4) {
+        const float hi = (float)c;
+        const float lo = (float)(c - (double)hi);
+        return fmaf(x, hi, x * lo);
+    } else {
+        return x * c;
+    }
+}
+// (a + ib) (cr + i ci) for a constant twiddle
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> kcmul(cpx<T> a, double cr, double ci) {
+    return mk(kmul(a.re, cr) - kmul(a.im, ci), kmul(a.re, ci) + kmul(a.im, cr));
+}
+
 // ------------------------------------------------------------------ small DFTs
 // v[k] <- sum_m v[m] exp(-+ 2 pi i m k / R)   (minus: forward, plus: INV)
 
@@ -67,11 +88,11 @@ __host__ __device__ __forceinline__ void dft2(cpx<T>* v) {
 
 template <typename T, bool INV>
 __host__ __device__ __forceinline__ void dft3(cpx<T>* v) {
-    const T h = T(0.5), s = T(0.86602540378443864676372317075294);  // sin(2 pi / 3)
+    const double s = 0.86602540378443864676372317075294;  // sin(2 pi / 3)
     cpx<T> t = v[1] + v[2];
     cpx<T> d = v[1] - v[2];
-    cpx<T> m = v[0] - scale(t, h);
-    cpx<T> r = rot90<T, INV>(scale(d, s));  // -+ i s (x1 - x2)
+    cpx<T> m = v[0] - scale(t, T(0.5));
+    cpx<T> r = rot90<T, INV>(mk(kmul(d.re, s), kmul(d.im, s)));  // -+ i s (x1 - x2)
     v[0] = v[0] + t;
     v[1] = m + r;
     v[2] = m - r;
@@ -89,17 +110,17 @@ __host__ __device__ __forceinline__ void dft4(cpx<T>* v) {
 
 template <typename T, bool INV>
 __host__ __device__ __forceinline__ void dft5(cpx<T>* v) {
-    const T c1 = T(0.30901699437494742410229341718282);   // cos(2 pi / 5)
-    const T c2 = T(-0.80901699437494742410229341718282);  // cos(4 pi / 5)
-    const T s1 = T(0.95105651629515357211643933337938);   // sin(2 pi / 5)
-    const T s2 = T(0.58778525229247312916870595463907);   // sin(4 pi / 5)
+    const double c1 = 0.30901699437494742410229341718282;   // cos(2 pi / 5)
+    const double c2 = -0.80901699437494742410229341718282;  // cos(4 pi / 5)
+    const double s1 = 0.95105651629515357211643933337938;   // sin(2 pi / 5)
+    const double s2 = 0.58778525229247312916870595463907;   // sin(4 pi / 5)
     cpx<T> a1 = v[1] + v[4], b1 = v[1] - v[4];
     cpx<T> a2 = v[2] + v[3], b2 = v[2] - v[3];
     cpx<T> x0 = v[0];
-    cpx<T> p1 = x0 + scale(a1, c1) + scale(a2, c2);
-    cpx<T> p2 = x0 + scale(a1, c2) + scale(a2, c1);
-    cpx<T> q1 = rot90<T, INV>(scale(b1, s1) + scale(b2, s2));  // -+ i (s1 b1 + s2 b2)
-    cpx<T> q2 = rot90<T, INV>(scale(b1, s2) - scale(b2, s1));  // -+ i (s2 b1 - s1 b2)
+    cpx<T> p1 = mk(x0.re + kmul(a1.re, c1) + kmul(a2.re, c2), x0.im + kmul(a1.im, c1) + kmul(a2.im, c2));
+    cpx<T> p2 = mk(x0.re + kmul(a1.re, c2) + kmul(a2.re, c1), x0.im + kmul(a1.im, c2) + kmul(a2.im, c1));
+    cpx<T> q1 = rot90<T, INV>(mk(kmul(b1.re, s1) + kmul(b2.re, s2), kmul(b1.im, s1) + kmul(b2.im, s2)));
+    cpx<T> q2 = rot90<T, INV>(mk(kmul(b1.re, s2) - kmul(b2.re, s1), kmul(b1.im, s2) - kmul(b2.im, s1)));
     v[0] = x0 + a1 + a2;
     v[1] = p1 + q1;
     v[4] = p1 - q1;
@@ -109,17 +130,17 @@ __host__ __device__ __forceinline__ void dft5(cpx<T>* v) {
 
 template <typename T, bool INV>
 __host__ __device__ __forceinline__ void dft8(cpx<T>* v) {
-    const T r = T(0.70710678118654752440084436210485);
+    const double r = 0.70710678118654752440084436210485;
     cpx<T> e[4] = {v[0], v[2], v[4], v[6]};
     cpx<T> o[4] = {v[1], v[3], v[5], v[7]};
     dft4<T, INV>(e);
     dft4<T, INV>(o);
     // w8^k = exp(-+ 2 pi i k / 8), k = 1, 2, 3
-    cpx<T> o1 = INV ? mk(r * (o[1].re - o[1].im), r * (o[1].re + o[1].im))
-                    : mk(r * (o[1].re + o[1].im), r * (o[1].im - o[1].re));
+    cpx<T> o1 = INV ? mk(kmul(o[1].re - o[1].im, r), kmul(o[1].re + o[1].im, r))
+                    : mk(kmul(o[1].re + o[1].im, r), kmul(o[1].im - o[1].re, r));
     cpx<T> o2 = rot90<T, INV>(o[2]);
-    cpx<T> o3 = INV ? mk(-r * (o[3].re + o[3].im), r * (o[3].re - o[3].im))
-                    : mk(r * (o[3].im - o[3].re), -r * (o[3].re + o[3].im));
+    cpx<T> o3 = INV ? mk(-kmul(o[3].re + o[3].im, r), kmul(o[3].re - o[3].im, r))
+                    : mk(kmul(o[3].im - o[3].re, r), -kmul(o[3].re + o[3].im, r));
     v[0] = e[0] + o[0];
     v[4] = e[0] - o[0];
     v[1] = e[1] + o1;
@@ -130,39 +151,71 @@ __host__ __device__ __forceinline__ void dft8(cpx<T>* v) {
     v[7] = e[3] - o3;
 }
 
+// Radix 16 and 32 from two halves of half the size and the twiddles
+// exp(-+ 2 pi i k / R) = cos(2 pi k / R) -+ i sin(2 pi k / R).
+template <typename T, int R, bool INV>
+__host__ __device__ __forceinline__ void dft_halves(cpx<T>* v);
+
 template <typename T, bool INV>
 __host__ __device__ __forceinline__ void dft16(cpx<T>* v) {
-    // cos / sin of pi k / 8, k = 0..7
-    const T C[8] = {T(1.0),
-                    T(0.92387953251128675612818318939679),
-                    T(0.70710678118654752440084436210485),
-                    T(0.38268343236508977172845998403040),
-                    T(0.0),
-                    T(-0.38268343236508977172845998403040),
-                    T(-0.70710678118654752440084436210485),
-                    T(-0.92387953251128675612818318939679)};
-    const T S[8] = {T(0.0),
-                    T(0.38268343236508977172845998403040),
-                    T(0.70710678118654752440084436210485),
-                    T(0.92387953251128675612818318939679),
-                    T(1.0),
-                    T(0.92387953251128675612818318939679),
-                    T(0.70710678118654752440084436210485),
-                    T(0.38268343236508977172845998403040)};
-    cpx<T> e[8], o[8];
+    dft_halves<T, 16, INV>(v);
+}
+template <typename T, bool INV>
+__host__ __device__ __forceinline__ void dft32(cpx<T>* v) {
+    dft_halves<T, 32, INV>(v);
+}
+
+template <typename T, int R, bool INV>
+__host__ __device__ __forceinline__ void dft_halves(cpx<T>* v) {
+    // cos(pi k / 16) and sin(pi k / 16), k = 0..16 (radix 32 uses every entry, radix 16 every second)
+    const double C[17] = {1.0,
+                          0.98078528040323044912618223613424,
+                          0.92387953251128675612818318939679,
+                          0.83146961230254523707878837761791,
+                          0.70710678118654752440084436210485,
+                          0.55557023301960222474283081394853,
+                          0.38268343236508977172845998403040,
+                          0.19509032201612826784828486847702,
+                          0.0,
+                          -0.19509032201612826784828486847702,
+                          -0.38268343236508977172845998403040,
+                          -0.55557023301960222474283081394853,
+                          -0.70710678118654752440084436210485,
+                          -0.83146961230254523707878837761791,
+                          -0.92387953251128675612818318939679,
+                          -0.98078528040323044912618223613424,
+                          -1.0};
+    constexpr int H = R / 2;
+    constexpr int step = 32 / R;  // index step into the pi/16 tables
+    cpx<T> e[H], o[H];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < H; ++m) {
         e[m] = v[2 * m];
         o[m] = v[2 * m + 1];
     }
-    dft8<T, INV>(e);
-    dft8<T, INV>(o);
+    if constexpr (H == 8) {
+        dft8<T, INV>(e);
+        dft8<T, INV>(o);
+    } else {
+        dft16<T, INV>(e);
+        dft16<T, INV>(o);
+    }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        cpx<T> w = mk(C[k], INV ? S[k] : -S[k]);
-        cpx<T> t = (k == 0) ? o[k] : o[k] * w;
+    for (int k = 0; k < H; ++k) {
+        cpx<T> t;
+        if (k == 0) {
+            t = o[0];
+        } else if (2 * k == H) {
+            t = rot90<T, INV>(o[k]);
+        } else {
+            // angle 2 pi k / R = pi (k step) / 16; sin(pi m / 16) = cos(pi (8 - m) / 16)
+            const int m = k * step;
+            const double c = C[m];
+            const double sn = m <= 8 ? C[8 - m] : C[m - 8];
+            t = kcmul(o[k], c, INV ? sn : -sn);
+        }
         v[k] = e[k] + t;
-        v[k + 8] = e[k] - t;
+        v[k + H] = e[k] - t;
     }
 }
 
@@ -174,6 +227,7 @@ __host__ __device__ __forceinline__ void dft(cpx<T>* v) {
     if constexpr (R == 5) dft5<T, INV>(v);
     if constexpr (R == 8) dft8<T, INV>(v);
     if constexpr (R == 16) dft16<T, INV>(v);
+    if constexpr (R == 32) dft32<T, INV>(v);
 }
 
 // ------------------------------------------------------------------ radix plans

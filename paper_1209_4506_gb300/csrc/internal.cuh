@@ -26,9 +26,9 @@ struct PoissonArgs {
     const cpx<T>* twa;  // exp(-2 pi i k / N1), k < N1
     const cpx<T>* twb;  // exp(-2 pi i k / N2)
     const cpx<T>* twc;  // exp(-2 pi i k / N3)   (the M-point transform uses every 2nd entry)
-    const T* gsqa;      // (2 pi k'/L1)^2, k' the signed frequency of k
-    const T* gsqb;
-    const T* gsqc;
+    const cpx<T>* gsqa;  // (2 pi k'/L1)^2 (k' the signed frequency of k) as high + low parts
+    const cpx<T>* gsqb;
+    const cpx<T>* gsqc;
     cpx<T>* W;          // half spectrum [N1][N2][ldc]
     T green_scale;      // 4 pi / N_tot (inverse-transform normalisation folded in)
     double* eh_partials;
@@ -40,14 +40,64 @@ struct PoissonArgs {
     int a_chunks;  // ceil(nh / a_cols)
 };
 
+// Twiddle exp(-2 pi i k / N) as a rounded value and its remainder (zero in FP64).
+template <typename T>
+struct TwPair {
+    cpx<T> h, l;
+};
+
+// Arguments of the specialised (compile-time radix) passes.
+template <typename T>
+struct FastArgs {
+    int n1, n2, n3, M, nh, ldc;
+    const TwPair<T>* twpa;  // N1 entries
+    const TwPair<T>* twpb;  // N2 entries
+    const TwPair<T>* twpc;  // N3 entries
+    const cpx<T>* gsqa;
+    const cpx<T>* gsqb;
+    const cpx<T>* gsqc;
+    cpx<T>* W;
+    T green_scale;
+    double* eh_partials;
+    int a_chunks, b_chunks;
+};
+
+// Sum of v over the block in FP64 (fixed order); the result is valid in thread 0.
+// `red` holds one double per warp.  Contains __syncthreads().
+__device__ __forceinline__ double block_sum_double(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    return s;
+}
+
+// Per-atom data prepared once per call (k_atom_prep): the cutoff box of the
+// atom in unwrapped grid indices and the offset of its first point, split in
+// a high and a low part so FP32 kernels can form d = (lo + m) h - X to full
+// FP32 accuracy without FP64 arithmetic.
+template <typename T>
+struct AtomPrep {
+    int lo[3];   // first unwrapped grid index of the box along a, b, c
+    int cnt[3];  // points of the box along a, b, c
+    T dh[3];     // lo h - X, rounded to T
+    T dl[3];     // (lo h - X) - dh (zero for FP64)
+    T qn;        // q (pi s^2)^(-3/2), formed in FP64 and rounded once
+};
+
 // Arguments of the splat and the force gather.
 template <typename T>
 struct AtomArgs {
     int n1, n2, n3;
     double h1, h2, h3;
+    T hh[3], hl[3];  // grid spacing split into high and low parts
     double L1, L2, L3;
     double rc;      // per-axis truncation radius (Bohr)
     double inv_s2;  // 1 / sigma^2
+    T is2h, is2l;   // 1 / sigma^2 split into high and low parts
     double norm;    // (pi sigma^2)^(-3/2)
     double dV;
     const double* pos;
@@ -55,7 +105,11 @@ struct AtomArgs {
     int n;          // atoms
     int apl;        // atoms per leaf
     int nleaves;
-    double* leaf_box;  // [nleaves][6]: lo xyz, hi xyz (unwrapped)
+    AtomPrep<T>* prep;  // [n]
+    T* fac;             // [n][3][fb]: exp(-d_m^2/s^2) at box point m of each axis
+    T* dfac;            // [n][3][fb]: d_m exp(-d_m^2/s^2)
+    int fb;             // row length of fac / dfac (largest box extent)
+    int* leaf;          // [nleaves][6]: start a, b, c (unwrapped), length a, b, c (points)
 };
 
 struct Plan {
@@ -71,10 +125,14 @@ struct Plan {
     void* W = nullptr;        // half spectrum
     void* R = nullptr;        // one real grid (forces recompute, host step)
     void* tw[3] = {nullptr, nullptr, nullptr};
+    void* twp[3] = {nullptr, nullptr, nullptr};  // TwPair tables
     void* gsq[3] = {nullptr, nullptr, nullptr};
     double* eh_partials = nullptr;
     int n_eh_partials = 0;
-    double* leaf_box = nullptr;
+    void* atom_prep = nullptr;  // AtomPrep<T>[max_atoms]
+    void* atom_fac = nullptr;   // T[max_atoms][3][box_max]
+    void* atom_dfac = nullptr;  // T[max_atoms][3][box_max]
+    int* leaf_box = nullptr;    // [max_leaves][6]
     double* force_partials = nullptr;
     int max_force_slabs = 0;
     int box_max = 0;          // largest per-axis point count of one atom's cutoff box
@@ -85,8 +143,27 @@ struct Plan {
     size_t bytes = 0;
     // tiling
     int c_lines, b_cols, a_cols;
+    int use_fast = 0;  // bit 0: c passes, bit 1: b passes, bit 2: a pass use the specialised kernels
     size_t smem_c, smem_b, smem_a;
 };
+
+// Let kernel `f` use all of the device's opt-in shared memory that its static
+// shared memory leaves free (the attribute is per kernel, so plans of any
+// size can coexist).
+template <typename K>
+inline cudaError_t allow_max_dynamic_smem(K* f, int optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+inline cudaError_t optin_smem(int* bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return e;
+}
 
 // launchers (poisson.cu / atoms.cu); return cudaSuccess or the launch error
 cudaError_t launch_poisson(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s);
@@ -94,6 +171,9 @@ cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int 
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
                           double* phi, cudaStream_t s);
 cudaError_t configure_poisson_kernels(const Plan& p);
+cudaError_t configure_fast_kernels(const Plan& p);
+int fast_pass_mask(const Plan& p);
+long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
 cudaError_t configure_atom_kernels(const Plan& p);
 
 }  // namespace hartree

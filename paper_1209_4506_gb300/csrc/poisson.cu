@@ -21,18 +21,6 @@ namespace hartree {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ double block_sum_double(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    return s;  // valid in thread 0
-}
-
 // ---------------------------------------------------------------- pass 1: c r2c
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_c_r2c(const T* __restrict__ rho, PoissonArgs<T> a) {
@@ -101,13 +89,16 @@ __global__ void __launch_bounds__(kThreads) k_a_green(PoissonArgs<T> a) {
     GlobalTile<T> g{a.W + (long long)ib * a.ldc + c0, (long long)a.n2 * a.ldc};
     cpx<T>* F = run_fft_to_smem<T, false>(a.rpa, g, A, B, CA, nc, a.twa, 1);
     // F[k1][col] now holds rho~(k1, ib, c0 + col).
-    const T gb = a.gsqb[ib];
+    const cpx<T> gb = a.gsqb[ib];
     T sum = T(0), comp = T(0);  // compensated per-thread partial of sum m |rho~|^2 / G^2
     for (int e = threadIdx.x; e < a.n1 * nc; e += blockDim.x) {
         const int col = e % nc, k1 = e / nc;
         const int k3 = c0 + col;
         const cpx<T> v = F[k1 * CA + col];
-        const T G2 = a.gsqa[k1] + gb + a.gsqc[k3];
+        // |G|^2 from the split tables: the high parts sum to within one rounding,
+        // the low parts restore the table rounding (no systematic error on 1/|G|^2)
+        const cpx<T> ga = a.gsqa[k1], gc = a.gsqc[k3];
+        const T G2 = ((ga.re + gb.re) + gc.re) + ((ga.im + gb.im) + gc.im);
         const T inv = (G2 > T(0)) ? T(1) / G2 : T(0);
         const T mult = (k3 == 0 || k3 == a.M) ? T(1) : T(2);
         const T term = mult * (v.re * v.re + v.im * v.im) * inv - comp;
@@ -116,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_a_green(PoissonArgs<T> a) {
         sum = t;
         F[k1 * CA + col] = scale(v, inv * a.green_scale);
     }
-    const double bs = block_sum_double<T>((double)sum - (double)comp, red);
+    const double bs = block_sum_double((double)sum - (double)comp, red);
     if (threadIdx.x == 0) a.eh_partials[blockIdx.x] = bs;
     __syncthreads();
     cpx<T>* other = (F == A) ? B : A;
@@ -161,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_eh_finalize(const double* __restri
     __shared__ double red[kThreads / 32];
     double s = 0.0;
     for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
-    const double t = block_sum_double<double>(s, red);
+    const double t = block_sum_double(s, red);
     if (threadIdx.x == 0) *eh = factor * t;
 }
 
@@ -180,9 +171,9 @@ PoissonArgs<T> make_args(const Plan& p) {
     a.twa = static_cast<const cpx<T>*>(p.tw[0]);
     a.twb = static_cast<const cpx<T>*>(p.tw[1]);
     a.twc = static_cast<const cpx<T>*>(p.tw[2]);
-    a.gsqa = static_cast<const T*>(p.gsq[0]);
-    a.gsqb = static_cast<const T*>(p.gsq[1]);
-    a.gsqc = static_cast<const T*>(p.gsq[2]);
+    a.gsqa = static_cast<const cpx<T>*>(p.gsq[0]);
+    a.gsqb = static_cast<const cpx<T>*>(p.gsq[1]);
+    a.gsqc = static_cast<const cpx<T>*>(p.gsq[2]);
     a.W = static_cast<cpx<T>*>(p.W);
     const double ntot = (double)p.n[0] * p.n[1] * p.n[2];
     a.green_scale = T(4.0 * 3.14159265358979323846 / ntot);
@@ -198,35 +189,38 @@ PoissonArgs<T> make_args(const Plan& p) {
 template <typename T>
 cudaError_t poisson_impl(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s) {
     PoissonArgs<T> a = make_args<T>(p);
+    const int fast = p.use_fast;
     const long long nlines = (long long)p.n[0] * p.n[1];
     const unsigned gc = (unsigned)((nlines + p.c_lines - 1) / p.c_lines);
     const unsigned gb = (unsigned)(p.n[0] * a.b_chunks);
     const unsigned ga = (unsigned)(p.n[1] * a.a_chunks);
-    k_c_r2c<T><<<gc, kThreads, p.smem_c, s>>>(static_cast<const T*>(rho), a);
-    k_b<T, false><<<gb, kThreads, p.smem_b, s>>>(a);
-    k_a_green<T><<<ga, kThreads, p.smem_a, s>>>(a);
-    k_b<T, true><<<gb, kThreads, p.smem_b, s>>>(a);
-    k_c_c2r<T><<<gc, kThreads, p.smem_c, s>>>(static_cast<T*>(vh), a);
+    if (fast & 1) launch_fast_pass(p, 0, rho, vh, s);
+    else k_c_r2c<T><<<gc, kThreads, p.smem_c, s>>>(static_cast<const T*>(rho), a);
+    if (fast & 2) launch_fast_pass(p, 1, rho, vh, s);
+    else k_b<T, false><<<gb, kThreads, p.smem_b, s>>>(a);
+    long long n_part = ga;
+    if (fast & 4) n_part = launch_fast_pass(p, 2, rho, vh, s);
+    else k_a_green<T><<<ga, kThreads, p.smem_a, s>>>(a);
+    if (fast & 2) launch_fast_pass(p, 3, rho, vh, s);
+    else k_b<T, true><<<gb, kThreads, p.smem_b, s>>>(a);
+    if (fast & 1) launch_fast_pass(p, 4, rho, vh, s);
+    else k_c_c2r<T><<<gc, kThreads, p.smem_c, s>>>(static_cast<T*>(vh), a);
     if (eh) {
         const double ntot = (double)p.n[0] * p.n[1] * p.n[2];
         const double factor = 2.0 * 3.14159265358979323846 * p.omega / (ntot * ntot);
-        k_eh_finalize<<<1, kThreads, 0, s>>>(p.eh_partials, (int)ga, factor, eh);
+        k_eh_finalize<<<1, kThreads, 0, s>>>(p.eh_partials, (int)n_part, factor, eh);
     }
     return cudaGetLastError();
 }
 
-// Allow every pass kernel the device's opt-in maximum of dynamic shared
-// memory, so plans of different sizes can coexist (the attribute is per kernel,
-// not per plan).
 template <typename T>
-cudaError_t configure_poisson(int max_smem) {
+cudaError_t configure_poisson(int optin) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_c_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_c_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_b<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_b<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_a_green<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    return cudaSuccess;
+    if ((e = allow_max_dynamic_smem(k_c_r2c<T>, optin))) return e;
+    if ((e = allow_max_dynamic_smem(k_c_c2r<T>, optin))) return e;
+    if ((e = allow_max_dynamic_smem(k_b<T, false>, optin))) return e;
+    if ((e = allow_max_dynamic_smem(k_b<T, true>, optin))) return e;
+    return allow_max_dynamic_smem(k_a_green<T>, optin);
 }
 
 }  // namespace
@@ -236,13 +230,12 @@ cudaError_t launch_poisson(const Plan& p, const void* rho, void* vh, double* eh,
 }
 
 cudaError_t configure_poisson_kernels(const Plan& p) {
-    int dev = 0, max_smem = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int optin = 0;
+    cudaError_t e = optin_smem(&optin);
     if (e != cudaSuccess) return e;
-    if (p.smem_a > (size_t)max_smem || p.smem_b > (size_t)max_smem || p.smem_c > (size_t)max_smem)
+    if (p.smem_a + 1024 > (size_t)optin || p.smem_b > (size_t)optin || p.smem_c > (size_t)optin)
         return cudaErrorInvalidConfiguration;
-    return p.prec == HARTREE_FP64 ? configure_poisson<double>(max_smem) : configure_poisson<float>(max_smem);
+    return p.prec == HARTREE_FP64 ? configure_poisson<double>(optin) : configure_poisson<float>(optin);
 }
 
 }  // namespace hartree
