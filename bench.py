@@ -1,0 +1,324 @@
+#!/usr/bin/env python3
+"""Benchmark of the grid-side Hartree step on GB300 (one JSON line on stdout).
+
+Workload: the 8x8x8 diamond supercell (4,096 Gaussian charges, sigma = 0.5 Bohr,
+a = 53.92 Bohr) on a 512^3 FP32 grid.  One step is the whole per-iteration hot
+path: density splat over the bisection-ordered atoms, the five-pass Poisson
+solve with the fused Green multiply and E_H reduction, and the adjoint force
+gather.  The atom reorder (modified recursive bisection) runs once per
+geometry before timing and is reported as reorder_ms.
+
+value: HBM yardstick bytes per step (40 N_tot, the five read+write sweeps of
+the Poisson solve) x steps / time, summed over ranks ("GB/s", higher is
+better).  ms_per_step, solve_ms and the per-kernel breakdown sit beside it.
+
+--impl reference times the FP64 CPU oracle (the reference for this build) on
+the host cores, on a bounded 256^3 sample of the same system.
+Multi-GPU: one replica per GPU (the single grid does not shard without an
+all-to-all; replicas run independent workloads), launched with torchrun.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Hartree solve ms & HBM GB/s at 512^3 fp32; batched/adjoint vs plain solve"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=30)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(threads):
+    """One oracle step (splat, Poisson, E_H, forces) on the 256^3 diamond sample; seconds."""
+    import oracle as O
+    from paper_1209_4506_gb300 import synth
+
+    O.set_threads(threads)
+    S = synth.config5()  # 4x4x4 diamond cell, 512 atoms, sigma 0.5, 256^3: the 512^3 system's density and width
+    t0 = time.perf_counter()
+    rho = O.splat(S.n, S.cell, S.sigma, S.pos, S.q, 5.0)
+    vh, eh, _, _ = O.poisson(S.cell, rho)
+    O.forces(S.n, S.cell, S.sigma, S.pos, S.q, vh, 5.0)
+    return time.perf_counter() - t0, S
+
+
+SAMPLE_TEXT = ("oracle step (splat 5 sigma, FP64 Poisson, E_H, forces) on the 4x4x4 diamond cell, 512 atoms, "
+               "256^3 grid (same density and sigma as the 512^3 workload); GB/s on its own 40 N_tot yardstick")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = len(os.sched_getaffinity(0))
+    for _ in range(args.warmup):
+        oracle_sample(threads)
+    times = []
+    for _ in range(args.steps):
+        t, S = oracle_sample(threads)
+        times.append(t)
+    total = sum(times)
+    ybytes = 40.0 * S.n_tot
+    value = ybytes * args.steps / total / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "diamond 4x4x4 supercell, 512 Gaussian charges, 256^3 grid (bounded sample of the "
+                               "512^3 diamond workload)", "grid": list(S.n), "atoms": S.n_atoms},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": SAMPLE_TEXT},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def kernel_traffic(name):
+    """ncu DRAM bytes per launch for `name`, if the capture matches the current source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        ent = d[name]
+        src = os.path.join(ROOT, ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return float(ent["bytes"]) if h == ent["sha256"] else None
+    except Exception:
+        return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1209_4506_gb300 import synth
+    from paper_1209_4506_gb300.hartree import HartreePlan, atoms_reorder
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    S = synth.config3a()
+    apl = 16
+    t0 = time.perf_counter()
+    perm, _ = atoms_reorder(S.pos, (S.n_atoms + apl - 1) // apl)
+    reorder_ms = 1e3 * (time.perf_counter() - t0)
+    pos_h, q_h = S.pos[perm], S.q[perm]
+    plan = HartreePlan(S.n, S.cell, S.sigma, "fp32", atoms_per_leaf=apl, max_atoms=S.n_atoms)
+    pos = torch.tensor(pos_h, device=dev)
+    q = torch.tensor(q_h, device=dev)
+    vh = torch.empty(S.n, dtype=torch.float32, device=dev)
+    rho = torch.empty(S.n, dtype=torch.float32, device=dev)
+    eh = torch.empty((), dtype=torch.float64, device=dev)
+    f = torch.empty((S.n_atoms, 3), dtype=torch.float64, device=dev)
+    ntot = S.n_tot
+    ybytes = 40.0 * ntot
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.step(pos, q, vh=vh, eh=eh, f=f)
+
+    sampler = ClockSampler(local)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)  # let the sampler attach before the timed region
+    launches0 = plan.launch_count
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = plan.launch_count - launches0
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = world * ybytes * args.steps / (t_ms * 1e-3) / 1e9
+
+    # per-kernel durations from CUDA events on the launching stream (same kernels, split calls)
+    names = ["splat", "pass0_c_r2c", "pass1_b_fwd", "pass2_a_green", "pass3_b_inv", "pass4_c_c2r", "forces"]
+    acc = {k: 0.0 for k in names}
+    reps = max(10, min(args.steps, 100))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+    for r in range(reps + 3):
+        ev[0].record(stream)
+        plan.splat(pos, q, rho)
+        ev[1].record(stream)
+        for p in range(5):
+            plan.solve_pass(p, rho=rho, vh=vh)
+            ev[2 + p].record(stream)
+        plan.forces(pos, q, vh=vh, f=f, want_phi=False)
+        ev[7].record(stream)
+        torch.cuda.synchronize()
+        if r >= 3:
+            for i, k in enumerate(names):
+                acc[k] += ev[i].elapsed_time(ev[i + 1])
+    kernels_ms = {k: acc[k] / reps for k in names}
+    solve_ms = sum(kernels_ms[k] for k in names[1:6])
+    # algorithmic bytes per launch (fp32): c passes read / write N real + N1 N2 (N3/2+1) complex, b / a read+write the
+    # half spectrum; splat writes N; forces read V once
+    half = 8.0 * S.n[0] * S.n[1] * (S.n[2] // 2 + 1)
+    alg = {"splat": 4.0 * ntot, "pass0_c_r2c": 4.0 * ntot + half, "pass1_b_fwd": 2 * half,
+           "pass2_a_green": 2 * half, "pass3_b_inv": 2 * half, "pass4_c_c2r": half + 4.0 * ntot,
+           "forces": 4.0 * ntot}
+    kernel_names = {"splat": "k_splat<float>", "pass0_c_r2c": "k_r2c_fast<float,16,256,16,16,1>",
+                    "pass1_b_fwd": "k_col_fast<float,16,512,8,8,8,0>", "pass2_a_green": "k_col_fast<float,16,512,8,8,8,2>",
+                    "pass3_b_inv": "k_col_fast<float,16,512,8,8,8,1>", "pass4_c_c2r": "k_c2r_fast<float,16,256,16,16,1>",
+                    "forces": "k_forces<float>"}
+    dom = max(names, key=lambda k: kernels_ms[k])
+    pk, src = peaks()
+    achieved = alg[dom] / (kernels_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": kernel_traffic(kernel_names[dom]),
+                "algorithmic_bytes": alg[dom], "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
+                if src == "measured" else "fallback 6.8 TB/s"}
+
+    # end to end through the C ABI with host buffers (pinned), copies and read-back inside the timed region
+    pos_pin = torch.tensor(pos_h).pin_memory()
+    q_pin = torch.tensor(q_h).pin_memory()
+    for _ in range(3):
+        plan.step_host(pos_pin.numpy(), q_pin.numpy())
+    n_e2e = max(10, min(args.steps, 100))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        plan.step_host(pos_pin.numpy(), q_pin.numpy())
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": world * ybytes * n_e2e / t_e2e / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": int(pos_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(8 + pos_h.nbytes),
+           "ms_per_step": 1e3 * t_e2e / n_e2e, "api": "hartree_step_host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = len(os.sched_getaffinity(0))
+        t_list = [oracle_sample(threads)[0] for _ in range(3)]
+        t_cpu = statistics.median(t_list)
+        cpu = {"value": 40.0 * 256 ** 3 / t_cpu / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+               "sample": SAMPLE_TEXT + f"; median of 3 steps, {t_cpu:.2f} s each"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "diamond 8x8x8 supercell, 4096 Gaussian charges (sigma 0.5 Bohr, cutoff 5 sigma), "
+                                   "512^3 grid, FP32: splat + Poisson + E_H + forces",
+                       "grid": list(S.n), "atoms": S.n_atoms, "yardstick_bytes_per_step": ybytes,
+                       "l2": "inputs larger than L2 (each grid array 0.5 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks, "solve_ms": solve_ms, "solve_gbs": ybytes / (solve_ms * 1e-3) / 1e9,
+            "kernels_ms": kernels_ms, "reorder_ms": reorder_ms, "eh": float(eh.item()),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

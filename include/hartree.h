@@ -155,6 +155,17 @@ int hartree_forces(hartree_plan plan, const double* pos, const double* q, int n,
                    double* phi, void* stream);
 
 /*
+ * The whole Hartree step on device buffers: splat, Poisson solve, E_H and the
+ * force gather, with the per-atom preparation done once.
+ *   pos, q  device [n][3] and [n] double
+ *   rho     device grid out, or NULL (rho then lives in vh until V_H overwrites it)
+ *   vh      device grid out;  eh device double out (may be NULL)
+ *   f       device [n][3] double out;  phi device [n] double out (may be NULL)
+ */
+int hartree_step(hartree_plan plan, const double* pos, const double* q, int n, void* rho, void* vh, double* eh,
+                 double* f, double* phi, void* stream);
+
+/*
  * End-to-end step on host buffers: copies pos and q to the device, runs
  * splat, solve and forces with V_H kept in the plan's grid buffer, copies E_H
  * (and forces when f is not NULL) back, and waits for the stream.
@@ -162,6 +173,22 @@ int hartree_forces(hartree_plan plan, const double* pos, const double* q, int n,
  */
 int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int n, double* eh, double* f,
                       void* stream);
+
+/* ---------------------------------------------------------------- introspection */
+
+/*
+ * One pass of the Poisson solve alone, for per-kernel timing and profiling.
+ * pass 0: c real-to-complex, rho -> the plan's half spectrum
+ * pass 1: b forward;  pass 2: a forward, 4 pi/|G|^2, E_H partial sums, a inverse
+ * pass 3: b inverse;  pass 4: c complex-to-real, half spectrum -> vh
+ * Calling passes 0..4 in order leaves in vh what hartree_solve_density leaves
+ * (the E_H reduction is not run).  rho is read by pass 0, vh written by pass 4;
+ * the other passes ignore both.  Returns HARTREE_ERR_INVALID for other pass ids.
+ */
+int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, void* stream);
+
+/* Number of CUDA kernels this plan has launched so far (host-side count). */
+unsigned long long hartree_plan_launch_count(hartree_plan plan);
 
 /* ---------------------------------------------------------------- errors */
 

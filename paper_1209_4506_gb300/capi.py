@@ -36,7 +36,10 @@ EXPORTED = (
     "hartree_solve_density",
     "hartree_solve",
     "hartree_forces",
+    "hartree_step",
     "hartree_step_host",
+    "hartree_solve_pass",
+    "hartree_plan_launch_count",
     "hartree_status_string",
     "hartree_last_error",
 )
@@ -87,7 +90,11 @@ def lib():
             L.hartree_solve_density.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.hartree_solve.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]
             L.hartree_forces.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]
+            L.hartree_step.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             L.hartree_step_host.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _vp]
+            L.hartree_solve_pass.argtypes = [_vp, _i, _vp, _vp, _vp]
+            L.hartree_plan_launch_count.argtypes = [_vp]
+            L.hartree_plan_launch_count.restype = ctypes.c_ulonglong
             L.hartree_status_string.argtypes = [_i]
             L.hartree_status_string.restype = ctypes.c_char_p
             L.hartree_last_error.argtypes = []
@@ -118,6 +125,9 @@ hartree_splat = _call("hartree_splat")
 hartree_solve_density = _call("hartree_solve_density")
 hartree_solve = _call("hartree_solve")
 hartree_forces = _call("hartree_forces")
+hartree_step = _call("hartree_step")
 hartree_step_host = _call("hartree_step_host")
+hartree_solve_pass = _call("hartree_solve_pass")
+hartree_plan_launch_count = _call("hartree_plan_launch_count")
 hartree_status_string = _call("hartree_status_string")
 hartree_last_error = _call("hartree_last_error")

@@ -10,9 +10,9 @@
 // index lo_d + m at offset d_m = (lo_d + m) h_d - X_d, and
 //   fac[m] = exp(-d_m^2/s^2),  dfac[m] = d_m exp(-d_m^2/s^2).
 // k_atom_prep finds the box; k_atom_factors fills the arrays once per call in
-// FP64 (three exponentials per atom and axis, then the exact ratio recurrence
-// f_{m+1} = f_m r_m, r_{m+1} = r_m exp(-2 h^2/s^2)) and rounds each value once,
-// so the FP32 splat and gather carry no exponential rounding bias.
+// FP64 (three exponentials per run of 8 box points, then the exact ratio
+// recurrence f_{m+1} = f_m r_m, r_{m+1} = r_m exp(-2 h^2/s^2)) and rounds each
+// value once, so the FP32 splat and gather carry no exponential rounding bias.
 //
 // k_leaf_boxes builds, for each leaf of `apl` consecutive atoms, the integer
 // box covering its atoms (structure C of Sec. 3.2.2: the parallelepiped
@@ -76,31 +76,41 @@ __global__ void k_atom_prep(AtomArgs<T> a) {
     a.prep[i] = p;
 }
 
-// One thread per (atom, axis): fac / dfac over the box, computed in FP64.
+// One thread per (atom, axis, run of kRun box points): fac / dfac computed in
+// FP64.  FP32 plans start each run with three exponentials and continue with
+// the exact ratio recurrence; FP64 plans evaluate every point directly.
+constexpr int kRun = 8;
+
 template <typename T>
 __global__ void k_atom_factors(AtomArgs<T> a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * a.n) return;
-    const int i = t / 3, d = t - 3 * i;
+    const int runs = (a.fb + kRun - 1) / kRun;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3LL * a.n * runs) return;
+    const int i = (int)(t / (3 * runs));
+    const int rem = (int)(t - (long long)i * 3 * runs);
+    const int d = rem / runs, m0 = (rem - d * runs) * kRun;
     const AtomPrep<T> p = a.prep[i];
+    const int cnt = p.cnt[d];
+    if (m0 >= cnt) return;
+    const int m1 = min(cnt, m0 + kRun);
     const double h = d == 0 ? a.h1 : (d == 1 ? a.h2 : a.h3);
     const double D0 = (double)p.dh[d] + (double)p.dl[d];  // lo h - X
     T* f = a.fac + ((long long)i * 3 + d) * a.fb;
     T* df = a.dfac + ((long long)i * 3 + d) * a.fb;
-    const int cnt = p.cnt[d];
     if constexpr (sizeof(T) == 8) {
-        for (int m = 0; m < cnt; ++m) {
+        for (int m = m0; m < m1; ++m) {
             const double dm = fma((double)m, h, D0);
             const double g = exp(-dm * dm * a.inv_s2);
             f[m] = g;
             df[m] = dm * g;
         }
     } else {
-        // exponent(m) = -(D0 + m h)^2 / s^2: successive ratios are exp(-(2 D0 h + (2m + 1) h^2) / s^2)
-        double g = exp(-D0 * D0 * a.inv_s2);
-        double r = exp(-(2.0 * D0 * h + h * h) * a.inv_s2);
+        // exponent(m) = -(D0 + m h)^2 / s^2: successive ratios are exp(-(2 d_m h + h^2) / s^2)
+        const double ds = fma((double)m0, h, D0);
+        double g = exp(-ds * ds * a.inv_s2);
+        double r = exp(-(2.0 * ds * h + h * h) * a.inv_s2);
         const double q = exp(-2.0 * h * h * a.inv_s2);
-        for (int m = 0; m < cnt; ++m) {
+        for (int m = m0; m < m1; ++m) {
             const double dm = fma((double)m, h, D0);
             f[m] = (T)g;
             df[m] = (T)(dm * g);
@@ -397,35 +407,49 @@ AtomArgs<T> make_atom_args(const Plan& p, const double* pos, const double* q, in
 }
 
 template <typename T>
-cudaError_t prep_atoms(const AtomArgs<T>& a, cudaStream_t s) {
+cudaError_t prep_atoms(const Plan& p, const AtomArgs<T>& a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
+    p.launches += 2;
     k_atom_prep<T><<<(a.n + 127) / 128, 128, 0, s>>>(a);
-    k_atom_factors<T><<<(3 * a.n + 127) / 128, 128, 0, s>>>(a);
+    const long long nt = 3LL * a.n * ((a.fb + kRun - 1) / kRun);
+    k_atom_factors<T><<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t splat_impl(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s) {
-    AtomArgs<T> a = make_atom_args<T>(p, pos, q, n);
-    cudaError_t e = prep_atoms<T>(a, s);
-    if (e != cudaSuccess) return e;
+cudaError_t splat_prepared(const Plan& p, const AtomArgs<T>& a, void* rho, cudaStream_t s) {
+    p.launches += (a.nleaves > 0 ? 1 : 0) + 1;
     if (a.nleaves > 0)
-        k_leaf_boxes<T><<<(a.nleaves + 127) / 128, 128, 0, s>>>(a.prep, n, p.apl, a.nleaves, p.n[0], p.n[1], p.n[2],
-                                                                p.leaf_box);
+        k_leaf_boxes<T><<<(a.nleaves + 127) / 128, 128, 0, s>>>(a.prep, a.n, p.apl, a.nleaves, p.n[0], p.n[1],
+                                                                p.n[2], p.leaf_box);
     const int tA = (p.n[0] + TA - 1) / TA, tB = (p.n[1] + TB - 1) / TB, tC = (p.n[2] + TC - 1) / TC;
     k_splat<T><<<(unsigned)tA * tB * tC, kThreads, 0, s>>>(a, static_cast<T*>(rho), tB, tC);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t splat_impl(const Plan& p, const double* pos, const double* q, int n, void* rho, bool prepared,
+                       cudaStream_t s) {
+    AtomArgs<T> a = make_atom_args<T>(p, pos, q, n);
+    if (!prepared) {
+        cudaError_t e = prep_atoms<T>(p, a, s);
+        if (e != cudaSuccess) return e;
+    }
+    return splat_prepared<T>(p, a, rho, s);
 }
 
 size_t forces_smem(const Plan& p, size_t real_size) { return 3 * (size_t)p.box_max * (2 * real_size + sizeof(int)); }
 
 template <typename T>
 cudaError_t forces_impl(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
-                        double* phi, cudaStream_t s) {
+                        double* phi, bool prepared, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     AtomArgs<T> a = make_atom_args<T>(p, pos, q, n);
-    cudaError_t e = prep_atoms<T>(a, s);
-    if (e != cudaSuccess) return e;
+    if (!prepared) {
+        cudaError_t e = prep_atoms<T>(p, a, s);
+        if (e != cudaSuccess) return e;
+    }
+    p.launches += 2;
     int slabs = (4 * 152 * 2 + n - 1) / n;  // enough CTAs to cover the GPU
     if (slabs > p.max_force_slabs) slabs = p.max_force_slabs;
     if (slabs < 1) slabs = 1;
@@ -450,14 +474,16 @@ cudaError_t configure_atom_kernels(const Plan& p) {
     return p.prec == HARTREE_FP64 ? configure_atoms<double>(optin) : configure_atoms<float>(optin);
 }
 
-cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s) {
-    return p.prec == HARTREE_FP64 ? splat_impl<double>(p, pos, q, n, rho, s) : splat_impl<float>(p, pos, q, n, rho, s);
+cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s,
+                         bool prepared) {
+    return p.prec == HARTREE_FP64 ? splat_impl<double>(p, pos, q, n, rho, prepared, s)
+                                  : splat_impl<float>(p, pos, q, n, rho, prepared, s);
 }
 
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
-                          double* phi, cudaStream_t s) {
-    return p.prec == HARTREE_FP64 ? forces_impl<double>(p, pos, q, n, vh, f, phi, s)
-                                  : forces_impl<float>(p, pos, q, n, vh, f, phi, s);
+                          double* phi, cudaStream_t s, bool prepared) {
+    return p.prec == HARTREE_FP64 ? forces_impl<double>(p, pos, q, n, vh, f, phi, prepared, s)
+                                  : forces_impl<float>(p, pos, q, n, vh, f, phi, prepared, s);
 }
 
 }  // namespace hartree

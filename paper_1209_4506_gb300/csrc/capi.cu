@@ -347,6 +347,29 @@ int hartree_forces(hartree_plan plan, const double* pos, const double* q, int n,
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "forces");
 }
 
+int hartree_step(hartree_plan plan, const double* pos, const double* q, int n, void* rho, void* vh, double* eh,
+                 double* f, double* phi, void* stream) {
+    if (!plan || !vh || (n > 0 && (!pos || !q || !f))) return fail(HARTREE_ERR_INVALID, "step: null argument");
+    if (n < 0 || n > plan->p.max_atoms)
+        return fail(HARTREE_ERR_INVALID, "step: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
+    cudaStream_t s = (cudaStream_t)stream;
+    void* dens = rho ? rho : vh;
+    cudaError_t e = launch_splat(plan->p, pos, q, n, dens, s);
+    if (e == cudaSuccess) e = launch_poisson(plan->p, dens, vh, eh, s);
+    if (e == cudaSuccess && n > 0) e = launch_forces(plan->p, pos, q, n, vh, f, phi, s, true);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "step");
+}
+
+int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, void* stream) {
+    if (!plan) return fail(HARTREE_ERR_INVALID, "solve_pass: null plan");
+    if (pass < 0 || pass > 4) return fail(HARTREE_ERR_INVALID, "solve_pass: pass %d not in 0..4", pass);
+    if ((pass == 0 && !rho) || (pass == 4 && !vh)) return fail(HARTREE_ERR_INVALID, "solve_pass: null grid");
+    cudaError_t e = launch_poisson_pass(plan->p, pass, rho, vh, (cudaStream_t)stream);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "solve_pass");
+}
+
+unsigned long long hartree_plan_launch_count(hartree_plan plan) { return plan ? plan->p.launches : 0ULL; }
+
 int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int n, double* eh, double* f,
                       void* stream) {
     if (!plan || !eh || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "step_host: null argument");
@@ -367,7 +390,7 @@ int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int
     }
     if (e == cudaSuccess) e = launch_splat(p, p.d_pos, p.d_q, n, p.R, s);
     if (e == cudaSuccess) e = launch_poisson(p, p.R, p.R, p.d_eh, s);
-    if (e == cudaSuccess && f && n > 0) e = launch_forces(p, p.d_pos, p.d_q, n, p.R, p.d_f, nullptr, s);
+    if (e == cudaSuccess && f && n > 0) e = launch_forces(p, p.d_pos, p.d_q, n, p.R, p.d_f, nullptr, s, true);
     if (e == cudaSuccess) e = cudaMemcpyAsync(eh, p.d_eh, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && f && n > 0)
         e = cudaMemcpyAsync(f, p.d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);

@@ -143,6 +143,7 @@ struct Plan {
     size_t bytes = 0;
     // tiling
     int c_lines, b_cols, a_cols;
+    mutable unsigned long long launches = 0;  // kernels launched (host-side count)
     int use_fast = 0;  // bit 0: c passes, bit 1: b passes, bit 2: a pass use the specialised kernels
     size_t smem_c, smem_b, smem_a;
 };
@@ -167,9 +168,13 @@ inline cudaError_t optin_smem(int* bytes) {
 
 // launchers (poisson.cu / atoms.cu); return cudaSuccess or the launch error
 cudaError_t launch_poisson(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s);
-cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s);
+cudaError_t launch_poisson_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
+// `prepared`: the per-atom boxes and factor arrays of these very positions are
+// already in the plan's workspace (an earlier launch on the same stream).
+cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s,
+                         bool prepared = false);
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
-                          double* phi, cudaStream_t s);
+                          double* phi, cudaStream_t s, bool prepared = false);
 cudaError_t configure_poisson_kernels(const Plan& p);
 cudaError_t configure_fast_kernels(const Plan& p);
 int fast_pass_mask(const Plan& p);

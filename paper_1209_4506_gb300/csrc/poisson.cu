@@ -186,29 +186,38 @@ PoissonArgs<T> make_args(const Plan& p) {
     return a;
 }
 
+// One pass; returns the number of CTAs of the a pass (its E_H partial count) for pass 2.
 template <typename T>
-cudaError_t poisson_impl(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s) {
+long long pass_impl(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s) {
+    const int bit = (pass == 0 || pass == 4) ? 1 : ((pass == 1 || pass == 3) ? 2 : 4);
+    ++p.launches;
+    if (p.use_fast & bit) return launch_fast_pass(p, pass, rho, vh, s);
     PoissonArgs<T> a = make_args<T>(p);
-    const int fast = p.use_fast;
     const long long nlines = (long long)p.n[0] * p.n[1];
     const unsigned gc = (unsigned)((nlines + p.c_lines - 1) / p.c_lines);
     const unsigned gb = (unsigned)(p.n[0] * a.b_chunks);
     const unsigned ga = (unsigned)(p.n[1] * a.a_chunks);
-    if (fast & 1) launch_fast_pass(p, 0, rho, vh, s);
-    else k_c_r2c<T><<<gc, kThreads, p.smem_c, s>>>(static_cast<const T*>(rho), a);
-    if (fast & 2) launch_fast_pass(p, 1, rho, vh, s);
-    else k_b<T, false><<<gb, kThreads, p.smem_b, s>>>(a);
-    long long n_part = ga;
-    if (fast & 4) n_part = launch_fast_pass(p, 2, rho, vh, s);
-    else k_a_green<T><<<ga, kThreads, p.smem_a, s>>>(a);
-    if (fast & 2) launch_fast_pass(p, 3, rho, vh, s);
-    else k_b<T, true><<<gb, kThreads, p.smem_b, s>>>(a);
-    if (fast & 1) launch_fast_pass(p, 4, rho, vh, s);
-    else k_c_c2r<T><<<gc, kThreads, p.smem_c, s>>>(static_cast<T*>(vh), a);
+    switch (pass) {
+        case 0: k_c_r2c<T><<<gc, kThreads, p.smem_c, s>>>(static_cast<const T*>(rho), a); return gc;
+        case 1: k_b<T, false><<<gb, kThreads, p.smem_b, s>>>(a); return gb;
+        case 2: k_a_green<T><<<ga, kThreads, p.smem_a, s>>>(a); return ga;
+        case 3: k_b<T, true><<<gb, kThreads, p.smem_b, s>>>(a); return gb;
+        default: k_c_c2r<T><<<gc, kThreads, p.smem_c, s>>>(static_cast<T*>(vh), a); return gc;
+    }
+}
+
+template <typename T>
+cudaError_t poisson_impl(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s) {
+    long long n_part = 0;
+    for (int pass = 0; pass < 5; ++pass) {
+        const long long g = pass_impl<T>(p, pass, rho, vh, s);
+        if (pass == 2) n_part = g;
+    }
     if (eh) {
         const double ntot = (double)p.n[0] * p.n[1] * p.n[2];
         const double factor = 2.0 * 3.14159265358979323846 * p.omega / (ntot * ntot);
         k_eh_finalize<<<1, kThreads, 0, s>>>(p.eh_partials, (int)n_part, factor, eh);
+        ++p.launches;
     }
     return cudaGetLastError();
 }
@@ -227,6 +236,14 @@ cudaError_t configure_poisson(int optin) {
 
 cudaError_t launch_poisson(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s) {
     return p.prec == HARTREE_FP64 ? poisson_impl<double>(p, rho, vh, eh, s) : poisson_impl<float>(p, rho, vh, eh, s);
+}
+
+cudaError_t launch_poisson_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s) {
+    if (p.prec == HARTREE_FP64)
+        pass_impl<double>(p, pass, rho, vh, s);
+    else
+        pass_impl<float>(p, pass, rho, vh, s);
+    return cudaGetLastError();
 }
 
 cudaError_t configure_poisson_kernels(const Plan& p) {

@@ -166,6 +166,38 @@ class HartreePlan:
                                        phi.data_ptr() if want_phi else None, _stream_handle(self.device)))
         return (f, phi) if want_phi else f
 
+    def step(self, pos, q, vh=None, eh=None, f=None, phi=None, rho=None, want_phi: bool = False):
+        """Splat + solve + E_H + forces in one call: (vh, eh, f[, phi])."""
+        torch = _torch()
+        pos, q, n = self._atoms(pos, q)
+        vh = self._grid(vh, "vh")
+        if rho is not None:
+            rho = self._grid(rho, "rho")
+        if eh is None:
+            eh = torch.empty((), dtype=torch.float64, device=self.device)
+        if f is None:
+            f = torch.empty((n, 3), dtype=torch.float64, device=self.device)
+        if want_phi and phi is None:
+            phi = torch.empty((n,), dtype=torch.float64, device=self.device)
+        capi.check(capi.hartree_step(self.handle, pos.data_ptr(), q.data_ptr(), n,
+                                     rho.data_ptr() if rho is not None else None, vh.data_ptr(), eh.data_ptr(),
+                                     f.data_ptr(), phi.data_ptr() if phi is not None else None,
+                                     _stream_handle(self.device)))
+        return (vh, eh, f, phi) if want_phi else (vh, eh, f)
+
+    def solve_pass(self, pass_id: int, rho=None, vh=None):
+        """Launch one Poisson pass alone (0: c r2c .. 4: c c2r); for timing and profiling."""
+        if rho is not None:
+            rho = self._grid(rho, "rho")
+        if vh is not None:
+            vh = self._grid(vh, "vh")
+        capi.check(capi.hartree_solve_pass(self.handle, int(pass_id), rho.data_ptr() if rho is not None else None,
+                                           vh.data_ptr() if vh is not None else None, _stream_handle(self.device)))
+
+    @property
+    def launch_count(self) -> int:
+        return int(capi.hartree_plan_launch_count(self.handle))
+
     def step_host(self, pos: np.ndarray, q: np.ndarray, forces: bool = True):
         """Host arrays in, (E_H, F or None) out; copies and waits inside the library."""
         pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))

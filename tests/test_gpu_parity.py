@@ -239,3 +239,33 @@ def test_repeat_runs_are_bitwise_deterministic():
     a = gpu_step(S, "fp32")
     b = gpu_step(S, "fp32")
     assert np.array_equal(a["vh"], b["vh"]) and a["eh"] == b["eh"] and np.array_equal(a["forces"], b["forces"])
+
+
+def test_step_entry_point_matches_separate_calls():
+    S, ref = oracle_cfg("cfg2")
+    plan = HartreePlan(S.n, S.cell, S.sigma, "fp32")
+    P, Q = dev(S.pos), dev(S.q)
+    vh, eh, f, phi = plan.step(P, Q, want_phi=True)
+    vh2, eh2 = plan.solve(P, Q)
+    f2, phi2 = plan.forces(P, Q, vh2)
+    torch.cuda.synchronize()
+    assert torch.equal(vh, vh2) and eh.item() == eh2.item()
+    assert torch.equal(f, f2) and torch.equal(phi, phi2)
+    assert np.max(np.abs(f.cpu().numpy() - ref["forces"])) <= TOL["fp32"]["f"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_single_passes_reproduce_solve_density(precision):
+    shape, cell = (48, 40, 60), (9.1, 7.7, 11.3)
+    rng = np.random.default_rng(5)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    rho = torch.tensor(rng.standard_normal(shape), dtype=dt, device="cuda")
+    plan = HartreePlan(shape, cell, 0.5, precision)
+    vh_ref, _ = plan.solve_density(rho)
+    vh = torch.empty_like(rho)
+    n0 = plan.launch_count
+    for p in range(5):
+        plan.solve_pass(p, rho=rho, vh=vh)
+    torch.cuda.synchronize()
+    assert plan.launch_count - n0 == 5
+    assert torch.equal(vh, vh_ref)
