@@ -190,6 +190,34 @@ int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, v
 /* Number of CUDA kernels this plan has launched so far (host-side count). */
 unsigned long long hartree_plan_launch_count(hartree_plan plan);
 
+/* ---------------------------------------------------------------- no device allocation */
+
+/*
+ * hartree_solve_density without a plan and without allocating device memory.
+ * The paper has no counterpart; this exists for callers that cannot call
+ * cudaMalloc -- applications that give all device memory to their own
+ * allocator or pool up front, and code paths where a device allocation is not
+ * allowed or would stall other work.  Creating a plan allocates its
+ * workspace; this call instead uses a fixed 8 MiB scratch array that the
+ * library declares at file scope, which every GPU that loads the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   desc  host pointer: grid, cell and precision (HARTREE_FP64 or HARTREE_FP32;
+ *         sigma, cutoff, atoms_per_leaf and max_atoms are ignored).  The grid
+ *         must fit the scratch: the half spectrum N1 N2 ceil16(N3/2 + 1) x 8
+ *         bytes (FP32; ceil8(N3/2 + 1) x 16 bytes in FP64) plus small tables
+ *         must stay within 8 MiB, e.g. 120^3 in FP32 or 64^3 in FP64; larger
+ *         grids return HARTREE_ERR_UNSUPPORTED_SIZE before any device work.
+ *   rho, vh, eh  as in hartree_solve_density (eh may be NULL).
+ * The first call on each device looks up the scratch array's address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and leaves the
+ * last call's contents in it, so calls that overlap on the GPU (two streams,
+ * two host threads) race: serialise them.  Results match
+ * hartree_solve_density within the precision's tolerance.
+ */
+int hartree_solve_density_noalloc(const hartree_desc* desc, const void* rho, void* vh, double* eh, void* stream);
+
 /* ---------------------------------------------------------------- errors */
 
 const char* hartree_status_string(int status);

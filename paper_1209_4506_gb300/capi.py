@@ -40,6 +40,7 @@ EXPORTED = (
     "hartree_step_host",
     "hartree_solve_pass",
     "hartree_plan_launch_count",
+    "hartree_solve_density_noalloc",
     "hartree_status_string",
     "hartree_last_error",
 )
@@ -95,6 +96,7 @@ def lib():
             L.hartree_solve_pass.argtypes = [_vp, _i, _vp, _vp, _vp]
             L.hartree_plan_launch_count.argtypes = [_vp]
             L.hartree_plan_launch_count.restype = ctypes.c_ulonglong
+            L.hartree_solve_density_noalloc.argtypes = [ctypes.POINTER(hartree_desc), _vp, _vp, _vp, _vp]
             L.hartree_status_string.argtypes = [_i]
             L.hartree_status_string.restype = ctypes.c_char_p
             L.hartree_last_error.argtypes = []
@@ -129,5 +131,6 @@ hartree_step = _call("hartree_step")
 hartree_step_host = _call("hartree_step_host")
 hartree_solve_pass = _call("hartree_solve_pass")
 hartree_plan_launch_count = _call("hartree_plan_launch_count")
+hartree_solve_density_noalloc = _call("hartree_solve_density_noalloc")
 hartree_status_string = _call("hartree_status_string")
 hartree_last_error = _call("hartree_last_error")

@@ -144,6 +144,8 @@ bool finite_pos(double x) { return std::isfinite(x); }
 
 }  // namespace
 
+void hartree::set_last_error(const char* msg) { g_last_error = msg; }
+
 extern "C" {
 
 const char* hartree_status_string(int status) {

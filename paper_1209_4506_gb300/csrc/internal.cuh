@@ -175,6 +175,7 @@ cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int 
                          bool prepared = false);
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
                           double* phi, cudaStream_t s, bool prepared = false);
+void set_last_error(const char* msg);  // the message hartree_last_error() returns on this thread
 cudaError_t configure_poisson_kernels(const Plan& p);
 cudaError_t configure_fast_kernels(const Plan& p);
 int fast_pass_mask(const Plan& p);
