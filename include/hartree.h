@@ -190,6 +190,32 @@ int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, v
 /* Number of CUDA kernels this plan has launched so far (host-side count). */
 unsigned long long hartree_plan_launch_count(hartree_plan plan);
 
+/*
+ * Device-side status of the plan's kernels: synchronises the device, then
+ * returns HARTREE_ERR_TIMEOUT if any bounded wait inside a kernel (an mbarrier
+ * of a TMA-streamed pass) gave up since the last call, else HARTREE_OK.  The
+ * error word is cleared by the call.  A timed-out kernel leaves its output
+ * incomplete but the CUDA context usable.
+ */
+int hartree_plan_device_status(hartree_plan plan);
+
+/* ---------------------------------------------------------------- autotuning */
+
+/*
+ * Kernel variants: each pass kind (0: the two c passes, 1: the two b passes,
+ * 2: the a pass) may have several compiled tile shapes (columns or lines per
+ * CTA and threads per CTA); for FP32 b and a passes of 256 or 512 points
+ * variant 2 is the persistent kernel that streams tiles with TMA bulk copies.  hartree_plan_autotune times every variant on the
+ * plan's own workspace (overwriting it; waits for the stream; not capturable)
+ * and keeps the fastest; choice[3] (host, may be NULL) receives the picks.
+ * hartree_plan_set_variants applies picks saved earlier (e.g. from a cache);
+ * out-of-range picks return HARTREE_ERR_INVALID.  Every variant applies the
+ * same operations to each element, so V_H is identical across variants; E_H
+ * sums its terms in a different grouping and agrees to rounding.
+ */
+int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice);
+int hartree_plan_set_variants(hartree_plan plan, const int* choice);
+
 /* ---------------------------------------------------------------- no device allocation */
 
 /*

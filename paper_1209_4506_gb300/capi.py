@@ -41,6 +41,9 @@ EXPORTED = (
     "hartree_solve_pass",
     "hartree_plan_launch_count",
     "hartree_solve_density_noalloc",
+    "hartree_plan_autotune",
+    "hartree_plan_set_variants",
+    "hartree_plan_device_status",
     "hartree_status_string",
     "hartree_last_error",
 )
@@ -97,6 +100,9 @@ def lib():
             L.hartree_plan_launch_count.argtypes = [_vp]
             L.hartree_plan_launch_count.restype = ctypes.c_ulonglong
             L.hartree_solve_density_noalloc.argtypes = [ctypes.POINTER(hartree_desc), _vp, _vp, _vp, _vp]
+            L.hartree_plan_autotune.argtypes = [_vp, _vp, _vp]
+            L.hartree_plan_set_variants.argtypes = [_vp, _vp]
+            L.hartree_plan_device_status.argtypes = [_vp]
             L.hartree_status_string.argtypes = [_i]
             L.hartree_status_string.restype = ctypes.c_char_p
             L.hartree_last_error.argtypes = []
@@ -132,5 +138,8 @@ hartree_step_host = _call("hartree_step_host")
 hartree_solve_pass = _call("hartree_solve_pass")
 hartree_plan_launch_count = _call("hartree_plan_launch_count")
 hartree_solve_density_noalloc = _call("hartree_solve_density_noalloc")
+hartree_plan_autotune = _call("hartree_plan_autotune")
+hartree_plan_set_variants = _call("hartree_plan_set_variants")
+hartree_plan_device_status = _call("hartree_plan_device_status")
 hartree_status_string = _call("hartree_status_string")
 hartree_last_error = _call("hartree_last_error")

@@ -339,19 +339,11 @@ __global__ void __launch_bounds__(kThreads) k_forces(AtomArgs<T> a, const T* __r
             kahan_add(sz, cz, f0[i] * pz);
         }
     }
-    double v4[4] = {(double)s0 - (double)c0, (double)sx - (double)cx, (double)sy - (double)cy,
-                    (double)sz - (double)cz};
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // four block sums: error-free FP32 warp steps, FP64 only across warps
+    const T vs[4] = {s0, sx, sy, sz}, ve[4] = {-c0, -cx, -cy, -cz};
     for (int c = 0; c < 4; ++c) {
-        double v = v4[c];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[c][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += red[threadIdx.x][w];
-        part[(long long)blockIdx.x * 4 + threadIdx.x] = s;
+        const double tot = block_sum_comp(vs[c], ve[c], red[c]);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * 4 + c] = tot;
     }
 }
 

@@ -135,7 +135,8 @@ int upload_tables(Plan& p) {
 void free_plan(Plan& p) {
     void* ptrs[] = {p.W,           p.R,        p.tw[0],         p.tw[1], p.tw[2], p.twp[0], p.twp[1], p.twp[2], p.gsq[0],
                     p.gsq[1],      p.gsq[2],   p.eh_partials,   p.leaf_box,
-                    p.atom_prep,   p.atom_fac, p.atom_dfac, p.force_partials, p.d_pos,   p.d_q,   p.d_f,   p.d_eh};
+                    p.atom_prep,   p.atom_fac, p.atom_dfac, p.force_partials, p.d_pos,   p.d_q,   p.d_f,   p.d_eh,
+                    p.d_err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -271,6 +272,7 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         {(void**)&p.d_q, (size_t)p.max_atoms * sizeof(double)},
         {(void**)&p.d_f, (size_t)p.max_atoms * 3 * sizeof(double)},
         {(void**)&p.d_eh, sizeof(double)},
+        {(void**)&p.d_err, sizeof(int)},
     };
     for (auto& a : allocs) {
         cudaError_t e = cudaMalloc(a.ptr, a.bytes);
@@ -284,6 +286,14 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         p.bytes += a.bytes;
     }
     int st = p.prec == HARTREE_FP64 ? upload_tables<double>(p) : upload_tables<float>(p);
+    if (st == HARTREE_OK) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaMemset(p.d_err, 0, sizeof(int));
+        if (e != cudaSuccess) st = cuda_fail(e, "plan_create: device query");
+        else prepare_tma(p);
+    }
     if (st == HARTREE_OK) {
         cudaError_t e = configure_poisson_kernels(p);
         if (e == cudaSuccess) e = configure_fast_kernels(p);
@@ -371,6 +381,76 @@ int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, v
 }
 
 unsigned long long hartree_plan_launch_count(hartree_plan plan) { return plan ? plan->p.launches : 0ULL; }
+
+int hartree_plan_device_status(hartree_plan plan) {
+    if (!plan) return fail(HARTREE_ERR_INVALID, "device_status: null plan");
+    int err = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&err, plan->p.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && err) e = cudaMemset(plan->p.d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "device_status");
+    if (err) return fail(HARTREE_ERR_TIMEOUT, "a bounded device wait gave up (error word %d)", err);
+    return HARTREE_OK;
+}
+
+int hartree_plan_set_variants(hartree_plan plan, const int* choice) {
+    if (!plan || !choice) return fail(HARTREE_ERR_INVALID, "set_variants: null argument");
+    for (int k = 0; k < 3; ++k)
+        if (choice[k] < 0 || choice[k] >= fast_variants(plan->p, k))
+            return fail(HARTREE_ERR_INVALID, "set_variants: pass kind %d has %d variants, got %d", k,
+                        fast_variants(plan->p, k), choice[k]);
+    for (int k = 0; k < 3; ++k) plan->p.var[k] = choice[k];
+    return HARTREE_OK;
+}
+
+// Time every kernel variant of each pass kind on the plan's own workspace and keep the fastest.
+int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice) {
+    if (!plan) return fail(HARTREE_ERR_INVALID, "autotune: null plan");
+    Plan& p = plan->p;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(HARTREE_ERR_NOT_CAPTURABLE, "autotune times kernels; it cannot be captured");
+    const size_t ntot = (size_t)p.n[0] * p.n[1] * p.n[2];
+    e = cudaMemsetAsync(p.R, 0, ntot * p.real_size, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.W, 0, (size_t)p.n[0] * p.n[1] * p.ldc * 2 * p.real_size, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    static const int passes[3][2] = {{0, 4}, {1, 3}, {2, 2}};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        const int nv = fast_variants(p, k);
+        if (nv <= 1) continue;
+        float best = 1e30f;
+        int best_v = 0;
+        for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+            p.var[k] = v;
+            for (int rep = 0; rep < 3; ++rep)  // warm-up
+                for (int q = 0; q < 2; ++q) launch_poisson_pass(p, passes[k][q], p.R, p.R, s);
+            e = cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 10; ++rep)
+                for (int q = 0; q < 2; ++q) launch_poisson_pass(p, passes[k][q], p.R, p.R, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        p.var[k] = best_v;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if (choice)
+        for (int k = 0; k < 3; ++k) choice[k] = p.var[k];
+    return HARTREE_OK;
+}
 
 int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int n, double* eh, double* f,
                       void* stream) {

@@ -9,20 +9,23 @@
 //     so one shared-memory tile (no ping-pong) holds the lines;
 //   * the first stage reads HBM directly and the last stage writes HBM
 //     directly (coalesced: columns for the b/a passes, lines for the c passes);
-//   * twiddles live in shared memory as FP32 high/low pairs, and butterfly
-//     constants are split the same way, so FP32 rounding carries no
-//     systematic magnitude bias into E_H.
+//   * twiddles live in shared memory as FP32 high/low pairs, and forward
+//     butterflies use them and split constants, so FP32 rounding carries no
+//     systematic magnitude bias into E_H; the inverse transforms only shape
+//     V_H and use the plain values.
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace hartree {
 
 namespace {
 
-template <typename T>
+// a w (or a conj(w) when inv).  COMP: FP32 product with the twiddle's low part.
+template <bool COMP = true, typename T>
 __device__ __forceinline__ cpx<T> twmul(cpx<T> a, const TwPair<T>& w, bool inv) {
     const T hi_im = inv ? -w.h.im : w.h.im;
     const T lo_im = inv ? -w.l.im : w.l.im;
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && COMP) {
         const float tr = a.re * w.l.re - a.im * lo_im;
         const float ti = a.re * lo_im + a.im * w.l.re;
         return mk(fmaf(a.re, w.h.re, fmaf(-a.im, hi_im, tr)), fmaf(a.re, hi_im, fmaf(a.im, w.h.re, ti)));
@@ -95,7 +98,7 @@ struct LineC2RIn {
         const cpx<T> x1 = x[k];
         const cpx<T> x2 = conjg(x[M - k]);
         const cpx<T> Ep = x1 + x2;
-        const cpx<T> Op = twmul(x1 - x2, tw[k], true);
+        const cpx<T> Op = twmul<false>(x1 - x2, tw[k], true);
         return mk(Ep.re - Op.im, Ep.im + Op.re);
     }
 };
@@ -126,9 +129,9 @@ __device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, 
         const int k = j % NS;
         if constexpr (NS > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[t][r] = twmul(v[t][r], TW[(k * r * (N / (NS * R))) * TWS], INV);
+            for (int r = 1; r < R; ++r) v[t][r] = twmul<!INV>(v[t][r], TW[(k * r * (N / (NS * R))) * TWS], INV);
         }
-        dft<T, R, INV>(v[t]);
+        dft<T, R, INV, !INV>(v[t]);
         const int o = (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -211,10 +214,126 @@ __global__ void __launch_bounds__(NT, min_ctas<NT>()) k_col_fast(FastArgs<T> a) 
             v = scale(v, inv * a.green_scale);
         };
         ftransform<T, R0, R1, R2, JSTEP, 1, false, false>(g, sm, sm, col, j0, TW, green);
-        const double bs = block_sum_double((double)sum - (double)comp, red);
+        const double bs = block_sum_comp(sum, -comp, red);
         if (threadIdx.x == 0) a.eh_partials[blockIdx.x] = bs;
         __syncthreads();
         ftransform<T, R0, R1, R2, JSTEP, 1, true, true>(sm, sm, g, col, j0, TW, NoPost{});
+    }
+}
+
+// ------------------------------------------------------------------ TMA-streamed b and a passes (FP32)
+// Persistent CTAs walk the tiles blockIdx.x, blockIdx.x + gridDim.x, ... through
+// a ring of NBUF shared-memory tile buffers.  Thread 0 keeps NBUF - 1 tile
+// loads in flight (cp.async.bulk.tensor, completion counted on one mbarrier
+// per buffer) while the CTA transforms the current tile in place, then writes
+// it back with a bulk tensor store and refills the buffer once the store has
+// read it.  No load or store instruction touches HBM from the threads
+// themselves, and memory traffic overlaps the butterflies of the other tiles.
+// A wait that does not complete within kSpinLimit probes sets the error word
+// and ends the CTA's loop (all threads agree through __syncthreads_and).
+template <int COLS, int NT, int R0, int R1, int R2, int MODE, int NBUF>
+__global__ void __launch_bounds__(NT, 1)
+    k_col_tma(FastArgs<float> a, const __grid_constant__ CUtensorMap tmap, int ntiles, int chunks, int* err) {
+    constexpr int N = R0 * R1 * R2;
+    constexpr int JSTEP = NT / COLS;
+    constexpr int BOXR = N < 256 ? N : 256;  // rows per bulk copy (box dimension limit 256)
+    constexpr int NBOX = N / BOXR;
+    constexpr uint32_t TILE_BYTES = (uint32_t)N * COLS * 8;
+    // All shared memory is dynamic (a static array would shift the dynamic base), and the tile
+    // buffers start on a 1024-byte boundary (bulk tensor copies need 128-byte aligned buffers).
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    cpx<float>* bufs = reinterpret_cast<cpx<float>*>(base);
+    TwPair<float>* TW = reinterpret_cast<TwPair<float>*>(bufs + NBUF * N * COLS);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(TW + N);
+    double* red = reinterpret_cast<double*>(mbar + NBUF);  // one double per warp
+    const TwPair<float>* twg = MODE == 2 ? a.twpa : a.twpb;
+    for (int k = threadIdx.x; k < N; k += NT) TW[k] = twg[k];
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&mbar[b], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int grid = gridDim.x;
+    // tile t: line (a index for the b pass, b index for the a pass) and first column
+    auto issue_load = [&](int t, int b) {
+        const int line = t / chunks, c0 = (t - line * chunks) * COLS;
+        cpx<float>* dst = bufs + b * N * COLS;
+        mbar_arrive_expect_tx(&mbar[b], TILE_BYTES);
+        for (int h = 0; h < NBOX; ++h) {
+            if (MODE == 2)
+                tma_load_3d(dst + h * BOXR * COLS, &tmap, &mbar[b], 2 * c0, line, h * BOXR);
+            else
+                tma_load_3d(dst + h * BOXR * COLS, &tmap, &mbar[b], 2 * c0, h * BOXR, line);
+        }
+    };
+    auto issue_store = [&](int t, int b) {
+        const int line = t / chunks, c0 = (t - line * chunks) * COLS;
+        const cpx<float>* src = bufs + b * N * COLS;
+        for (int h = 0; h < NBOX; ++h) {
+            if (MODE == 2)
+                tma_store_3d(&tmap, src + h * BOXR * COLS, 2 * c0, line, h * BOXR);
+            else
+                tma_store_3d(&tmap, src + h * BOXR * COLS, 2 * c0, h * BOXR, line);
+        }
+        tma_commit();
+    };
+    if (threadIdx.x == 0)
+        for (int b = 0; b < NBUF; ++b) {
+            const int t = blockIdx.x + b * grid;
+            if (t < ntiles) issue_load(t, b);
+        }
+    const int col = threadIdx.x % COLS, j0 = threadIdx.x / COLS;
+    uint32_t parity = 0;
+    float sum = 0.f, comp = 0.f;
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * grid;
+        if (t >= ntiles) break;
+        const int b = k % NBUF;
+        const bool ok = mbar_wait(&mbar[b], (parity >> b) & 1u, err);
+        if (!__syncthreads_and(ok)) break;
+        parity ^= 1u << b;
+        ColSmem<float, COLS> sm{bufs + b * N * COLS};
+        if constexpr (MODE != 2) {
+            ftransform<float, R0, R1, R2, JSTEP, 1, MODE == 1, true>(sm, sm, sm, col, j0, TW, NoPost{});
+        } else {
+            const int line = t / chunks, c0 = (t - line * chunks) * COLS;
+            const int nc = min(COLS, a.nh - c0);
+            const cpx<float> gb = a.gsqb[line];
+            const int k3 = c0 + col;
+            const cpx<float> gc = a.gsqc[k3 < a.nh ? k3 : 0];
+            const float mult = (k3 == 0 || k3 == a.M) ? 1.f : 2.f;
+            auto green = [&](int c, int k1, cpx<float>& v) {
+                const cpx<float> ga = a.gsqa[k1];
+                const float G2 = ((ga.re + gb.re) + gc.re) + ((ga.im + gb.im) + gc.im);
+                const float inv = (G2 > 0.f) ? 1.f / G2 : 0.f;
+                if (c < nc) {
+                    const float term = mult * (v.re * v.re + v.im * v.im) * inv - comp;
+                    const float tt = sum + term;
+                    comp = (tt - sum) - term;
+                    sum = tt;
+                }
+                v = scale(v, inv * a.green_scale);
+            };
+            ftransform<float, R0, R1, R2, JSTEP, 1, false, true>(sm, sm, sm, col, j0, TW, green);
+            __syncthreads();
+            ftransform<float, R0, R1, R2, JSTEP, 1, true, true>(sm, sm, sm, col, j0, TW, NoPost{});
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            issue_store(t, b);
+            const int tn = blockIdx.x + (k + NBUF) * grid;
+            if (tn < ntiles) {
+                tma_wait_read<0>();  // the buffer is free once the store has read it
+                issue_load(tn, b);
+            }
+        }
+    }
+    if (threadIdx.x == 0) tma_wait_all();
+    if constexpr (MODE == 2) {
+        const double bs = block_sum_comp(sum, -comp, red);
+        if (threadIdx.x == 0) a.eh_partials[blockIdx.x] = bs;
     }
 }
 
@@ -310,36 +429,93 @@ struct LineCfg {
     }
 };
 
-// Column-pass configurations by line length (FP32 rows of 16 complex = 128 B; FP64 rows of 8).
+// TMA-streamed column pass configuration (FP32): 16 columns (128-byte rows) per tile.
+template <int NT, int R0, int R1, int R2, int NBUF>
+struct ColTmaCfg {
+    static constexpr int cols = 16, n = R0 * R1 * R2;
+    static size_t smem() {  // tile ring, twiddles, mbarriers, reduction slots, alignment slack
+        return (size_t)NBUF * n * 16 * sizeof(cpx<float>) + (size_t)n * sizeof(TwPair<float>) + NBUF * 8 +
+               (NT / 32) * sizeof(double) + 1024;
+    }
+    static cudaError_t configure(int optin) {
+        cudaError_t e;
+        if ((e = allow_max_dynamic_smem(k_col_tma<16, NT, R0, R1, R2, 0, NBUF>, optin))) return e;
+        if ((e = allow_max_dynamic_smem(k_col_tma<16, NT, R0, R1, R2, 1, NBUF>, optin))) return e;
+        return allow_max_dynamic_smem(k_col_tma<16, NT, R0, R1, R2, 2, NBUF>, optin);
+    }
+    static void launch(int mode, unsigned grid, const FastArgs<float>& a, const CUtensorMap& map, int ntiles,
+                       int chunks, int* err, cudaStream_t s) {
+        if (mode == 0) k_col_tma<16, NT, R0, R1, R2, 0, NBUF><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+        if (mode == 1) k_col_tma<16, NT, R0, R1, R2, 1, NBUF><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+        if (mode == 2) k_col_tma<16, NT, R0, R1, R2, 2, NBUF><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+    }
+};
+
+template <class F>
+bool with_col_tma_cfg(int n, F&& f) {
+    switch (n) {
+        case 256: f(ColTmaCfg<256, 16, 16, 1, 3>{}); return true;
+        case 512: f(ColTmaCfg<512, 8, 8, 8, 3>{}); return true;
+        default: return false;
+    }
+}
+
+// Column-pass configurations by line length and variant.  Variant 0: rows of
+// 128 bytes (16 FP32 / 8 FP64 complex columns per CTA); variant 1: half the
+// columns and threads per CTA, so twice as many CTAs share an SM.
 template <typename T, class F>
-bool with_col_cfg(int n, F&& f) {
+bool with_col_cfg(int n, int variant, F&& f) {
     constexpr bool d = sizeof(T) == 8;
+    const bool v1 = variant == 1;
     switch (n) {
         case 16: f(ColCfg<T, d ? 16 : 32, d ? 64 : 128, 4, 4, 1>{}); return true;
         case 32: f(ColCfg<T, d ? 16 : 32, d ? 64 : 128, 8, 4, 1>{}); return true;
         case 64: f(ColCfg<T, d ? 8 : 16, d ? 64 : 128, 8, 8, 1>{}); return true;
         case 128: f(ColCfg<T, d ? 8 : 16, d ? 64 : 128, 16, 8, 1>{}); return true;
-        case 256: f(ColCfg<T, d ? 8 : 16, d ? 128 : 256, 16, 16, 1>{}); return true;
-        case 512: f(ColCfg<T, d ? 8 : 16, d ? 256 : 512, 8, 8, 8>{}); return true;
+        case 256:
+            if (v1) f(ColCfg<T, d ? 4 : 8, d ? 64 : 128, 16, 16, 1>{});
+            else f(ColCfg<T, d ? 8 : 16, d ? 128 : 256, 16, 16, 1>{});
+            return true;
+        case 512:
+            if (v1) f(ColCfg<T, d ? 4 : 8, d ? 128 : 256, 8, 8, 8>{});
+            else f(ColCfg<T, d ? 8 : 16, d ? 256 : 512, 8, 8, 8>{});
+            return true;
         case 1024: f(ColCfg<T, 8, 512, 16, 8, 8>{}); return true;
         default: return false;
     }
 }
+int col_variants(int n) { return (n == 256 || n == 512) ? 2 : 1; }
 
-// c-pass configurations by M = N3 / 2.
+// Variant 2 of the b / a passes: the TMA-streamed kernel (FP32, plan has the tensor maps).
+bool col_tma_available(const Plan& p, int axis) {
+    return p.prec != HARTREE_FP64 && p.tma_ok && with_col_tma_cfg(p.n[axis], [](auto) {});
+}
+
+// c-pass configurations by M = N3 / 2 and variant (variant 1: half the lines per CTA).
 template <typename T, class F>
-bool with_line_cfg(int m, F&& f) {
+bool with_line_cfg(int m, int variant, F&& f) {
+    const bool v1 = variant == 1;
     switch (m) {
         case 16: f(LineCfg<T, 32, 128, 4, 4, 1>{}); return true;
         case 32: f(LineCfg<T, 32, 128, 8, 4, 1>{}); return true;
         case 64: f(LineCfg<T, 16, 128, 8, 8, 1>{}); return true;
-        case 128: f(LineCfg<T, 16, 128, 16, 8, 1>{}); return true;
-        case 256: f(LineCfg<T, 16, 256, 16, 16, 1>{}); return true;
-        case 512: f(LineCfg<T, 4, 256, 8, 8, 8>{}); return true;
+        case 128:
+            if (v1) f(LineCfg<T, 8, 64, 16, 8, 1>{});
+            else f(LineCfg<T, 16, 128, 16, 8, 1>{});
+            return true;
+        case 256:
+            if (v1) f(LineCfg<T, 8, 128, 16, 16, 1>{});
+            else f(LineCfg<T, 16, 256, 16, 16, 1>{});
+            return true;
+        case 512:
+            if (v1) f(LineCfg<T, 2, 128, 8, 8, 8>{});
+            else f(LineCfg<T, 4, 256, 8, 8, 8>{});
+            return true;
         case 1024: f(LineCfg<T, 4, 256, 16, 8, 8>{}); return true;
         default: return false;
     }
 }
+int line_variants(int m) { return (m == 128 || m == 256 || m == 512) ? 2 : 1; }
 
 template <typename T>
 FastArgs<T> make_fast_args(const Plan& p) {
@@ -361,8 +537,8 @@ FastArgs<T> make_fast_args(const Plan& p) {
     a.eh_partials = p.eh_partials;
     a.a_chunks = 1;
     a.b_chunks = 1;
-    with_col_cfg<T>(p.n[0], [&](auto c) { a.a_chunks = (p.nh + c.cols - 1) / c.cols; });
-    with_col_cfg<T>(p.n[1], [&](auto c) { a.b_chunks = (p.nh + c.cols - 1) / c.cols; });
+    with_col_cfg<T>(p.n[0], p.var[2], [&](auto c) { a.a_chunks = (p.nh + c.cols - 1) / c.cols; });
+    with_col_cfg<T>(p.n[1], p.var[1], [&](auto c) { a.b_chunks = (p.nh + c.cols - 1) / c.cols; });
     return a;
 }
 
@@ -372,9 +548,9 @@ FastArgs<T> make_fast_args(const Plan& p) {
 template <typename T>
 int fast_pass_mask_t(const Plan& p) {
     int m = 0;
-    if (with_line_cfg<T>(p.M, [](auto) {})) m |= 1;
-    if (with_col_cfg<T>(p.n[1], [](auto) {})) m |= 2;
-    if (with_col_cfg<T>(p.n[0], [](auto) {})) m |= 4;
+    if (with_line_cfg<T>(p.M, 0, [](auto) {})) m |= 1;
+    if (with_col_cfg<T>(p.n[1], 0, [](auto) {})) m |= 2;
+    if (with_col_cfg<T>(p.n[0], 0, [](auto) {})) m |= 4;
     return m;
 }
 
@@ -389,9 +565,13 @@ cudaError_t configure_fast_t(const Plan& p, int optin) {
         if (e == cudaSuccess && c.smem() + 2048 > (size_t)optin) e = cudaErrorInvalidConfiguration;
         if (e == cudaSuccess) e = c.configure(optin);
     };
-    with_line_cfg<T>(p.M, cfg);
-    with_col_cfg<T>(p.n[1], cfg);
-    with_col_cfg<T>(p.n[0], cfg);
+    for (int v = 0; v < line_variants(p.M); ++v) with_line_cfg<T>(p.M, v, cfg);
+    for (int v = 0; v < col_variants(p.n[1]); ++v) with_col_cfg<T>(p.n[1], v, cfg);
+    for (int v = 0; v < col_variants(p.n[0]); ++v) with_col_cfg<T>(p.n[0], v, cfg);
+    if constexpr (sizeof(T) == 4) {
+        if (col_tma_available(p, 1)) with_col_tma_cfg(p.n[1], cfg);
+        if (col_tma_available(p, 0)) with_col_tma_cfg(p.n[0], cfg);
+    }
     return e;
 }
 
@@ -409,27 +589,90 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
     FastArgs<T> a = make_fast_args<T>(p);
     long long grid = -1;
     if (pass == 0 || pass == 4) {
-        with_line_cfg<T>(p.M, [&](auto c) {
+        with_line_cfg<T>(p.M, p.var[0], [&](auto c) {
             grid = ((long long)p.n[0] * p.n[1] + c.lines - 1) / c.lines;
             c.launch(pass == 4, (unsigned)grid, rho, vh, a, s);
         });
-    } else if (pass == 1 || pass == 3) {
-        with_col_cfg<T>(p.n[1], [&](auto c) {
-            grid = (long long)p.n[0] * a.b_chunks;
-            c.launch(pass == 3 ? 1 : 0, (unsigned)grid, a, s);
-        });
-    } else {
-        with_col_cfg<T>(p.n[0], [&](auto c) {
-            grid = (long long)p.n[1] * a.a_chunks;
-            c.launch(2, (unsigned)grid, a, s);
-        });
+        return grid;
     }
+    const int axis = (pass == 2) ? 0 : 1;  // transformed axis: a for pass 2, b for passes 1 and 3
+    const int kind = (pass == 2) ? 2 : 1;
+    if constexpr (sizeof(T) == 4) {
+        if (p.var[kind] == 2 && col_tma_available(p, axis)) {
+            // variant 2: TMA-streamed persistent kernel, one CTA per SM
+            with_col_tma_cfg(p.n[axis], [&](auto c) {
+                const int chunks = (p.nh + c.cols - 1) / c.cols;
+                const int ntiles = p.n[1 - axis] * chunks;
+                grid = ntiles < p.sm_count ? ntiles : p.sm_count;
+                c.launch(pass == 1 ? 0 : (pass == 3 ? 1 : 2), (unsigned)grid, a, axis == 0 ? p.tmap_a : p.tmap_b,
+                         ntiles, chunks, p.d_err, s);
+            });
+            return grid;
+        }
+    }
+    with_col_cfg<T>(p.n[axis], p.var[kind], [&](auto c) {
+        grid = (long long)p.n[1 - axis] * (axis == 0 ? a.a_chunks : a.b_chunks);
+        c.launch(pass == 2 ? 2 : (pass == 3 ? 1 : 0), (unsigned)grid, a, s);
+    });
     return grid;
 }
 
 long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s) {
     return p.prec == HARTREE_FP64 ? launch_fast_pass_t<double>(p, pass, rho, vh, s)
                                   : launch_fast_pass_t<float>(p, pass, rho, vh, s);
+}
+
+int fast_variants(const Plan& p, int kind) {
+    if (kind == 0) return (p.use_fast & 1) ? line_variants(p.M) : 1;
+    if (kind == 1) return (p.use_fast & 2) ? (col_tma_available(p, 1) ? 3 : col_variants(p.n[1])) : 1;
+    return (p.use_fast & 4) ? (col_tma_available(p, 0) ? 3 : col_variants(p.n[0])) : 1;
+}
+
+// ------------------------------------------------------------------ host: tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+bool encode_tensor_map_3d(CUtensorMap* map, void* base, const uint64_t dims[3], const uint64_t strides[2],
+                          const uint32_t box[3]) {
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t gd[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t gs[2] = {strides[0], strides[1]};
+    const cuuint32_t bd[3] = {box[0], box[1], box[2]};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, gd, gs, bd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps over the half spectrum W (FP32, viewed as floats [N1][N2][2 ldc]) for the b and a
+// column passes: boxes of 16 complex columns by up to 256 rows.
+void prepare_tma(Plan& p) {
+    p.tma_ok = false;
+    if (p.prec == HARTREE_FP64) return;
+    const uint64_t dims[3] = {(uint64_t)2 * p.ldc, (uint64_t)p.n[1], (uint64_t)p.n[0]};
+    const uint64_t strides[2] = {(uint64_t)2 * p.ldc * 4, (uint64_t)p.n[1] * 2 * p.ldc * 4};
+    const uint32_t box_b[3] = {32, (uint32_t)(p.n[1] < 256 ? p.n[1] : 256), 1};
+    const uint32_t box_a[3] = {32, 1, (uint32_t)(p.n[0] < 256 ? p.n[0] : 256)};
+    const bool ok_b = encode_tensor_map_3d(&p.tmap_b, p.W, dims, strides, box_b);
+    const bool ok_a = encode_tensor_map_3d(&p.tmap_a, p.W, dims, strides, box_a);
+    p.tma_ok = ok_a && ok_b && p.d_err != nullptr && p.sm_count > 0;
 }
 
 }  // namespace hartree

@@ -60,45 +60,45 @@ __host__ __device__ __forceinline__ cpx<T> rot90(cpx<T> a) {
 // a rounded high part and the remainder, so the constant carries no rounding
 // bias: a single-rounded sqrt(1/2) shrinks |w| below 1 at every radix-8
 // stage, which shows up as a systematic loss of spectral energy (E_H).
-template <typename T>
+template <typename T, bool COMP = true>
 __host__ __device__ __forceinline__ T kmul(T x, double c) {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && COMP) {
         const float hi = (float)c;
         const float lo = (float)(c - (double)hi);
         return fmaf(x, hi, x * lo);
     } else {
-        return x * c;
+        return x * (T)c;
     }
 }
 // (a + ib) (cr + i ci) for a constant twiddle
-template <typename T>
+template <typename T, bool COMP = true>
 __host__ __device__ __forceinline__ cpx<T> kcmul(cpx<T> a, double cr, double ci) {
-    return mk(kmul(a.re, cr) - kmul(a.im, ci), kmul(a.re, ci) + kmul(a.im, cr));
+    return mk(kmul<T, COMP>(a.re, cr) - kmul<T, COMP>(a.im, ci), kmul<T, COMP>(a.re, ci) + kmul<T, COMP>(a.im, cr));
 }
 
 // ------------------------------------------------------------------ small DFTs
 // v[k] <- sum_m v[m] exp(-+ 2 pi i m k / R)   (minus: forward, plus: INV)
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool COMP = true>
 __host__ __device__ __forceinline__ void dft2(cpx<T>* v) {
     cpx<T> a = v[0], b = v[1];
     v[0] = a + b;
     v[1] = a - b;
 }
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool COMP = true>
 __host__ __device__ __forceinline__ void dft3(cpx<T>* v) {
     const double s = 0.86602540378443864676372317075294;  // sin(2 pi / 3)
     cpx<T> t = v[1] + v[2];
     cpx<T> d = v[1] - v[2];
     cpx<T> m = v[0] - scale(t, T(0.5));
-    cpx<T> r = rot90<T, INV>(mk(kmul(d.re, s), kmul(d.im, s)));  // -+ i s (x1 - x2)
+    cpx<T> r = rot90<T, INV>(mk(kmul<T, COMP>(d.re, s), kmul<T, COMP>(d.im, s)));  // -+ i s (x1 - x2)
     v[0] = v[0] + t;
     v[1] = m + r;
     v[2] = m - r;
 }
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool COMP = true>
 __host__ __device__ __forceinline__ void dft4(cpx<T>* v) {
     cpx<T> s02 = v[0] + v[2], d02 = v[0] - v[2];
     cpx<T> s13 = v[1] + v[3], d13 = rot90<T, INV>(v[1] - v[3]);
@@ -108,7 +108,7 @@ __host__ __device__ __forceinline__ void dft4(cpx<T>* v) {
     v[3] = d02 - d13;
 }
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool COMP = true>
 __host__ __device__ __forceinline__ void dft5(cpx<T>* v) {
     const double c1 = 0.30901699437494742410229341718282;   // cos(2 pi / 5)
     const double c2 = -0.80901699437494742410229341718282;  // cos(4 pi / 5)
@@ -117,10 +117,10 @@ __host__ __device__ __forceinline__ void dft5(cpx<T>* v) {
     cpx<T> a1 = v[1] + v[4], b1 = v[1] - v[4];
     cpx<T> a2 = v[2] + v[3], b2 = v[2] - v[3];
     cpx<T> x0 = v[0];
-    cpx<T> p1 = mk(x0.re + kmul(a1.re, c1) + kmul(a2.re, c2), x0.im + kmul(a1.im, c1) + kmul(a2.im, c2));
-    cpx<T> p2 = mk(x0.re + kmul(a1.re, c2) + kmul(a2.re, c1), x0.im + kmul(a1.im, c2) + kmul(a2.im, c1));
-    cpx<T> q1 = rot90<T, INV>(mk(kmul(b1.re, s1) + kmul(b2.re, s2), kmul(b1.im, s1) + kmul(b2.im, s2)));
-    cpx<T> q2 = rot90<T, INV>(mk(kmul(b1.re, s2) - kmul(b2.re, s1), kmul(b1.im, s2) - kmul(b2.im, s1)));
+    cpx<T> p1 = mk(x0.re + kmul<T, COMP>(a1.re, c1) + kmul<T, COMP>(a2.re, c2), x0.im + kmul<T, COMP>(a1.im, c1) + kmul<T, COMP>(a2.im, c2));
+    cpx<T> p2 = mk(x0.re + kmul<T, COMP>(a1.re, c2) + kmul<T, COMP>(a2.re, c1), x0.im + kmul<T, COMP>(a1.im, c2) + kmul<T, COMP>(a2.im, c1));
+    cpx<T> q1 = rot90<T, INV>(mk(kmul<T, COMP>(b1.re, s1) + kmul<T, COMP>(b2.re, s2), kmul<T, COMP>(b1.im, s1) + kmul<T, COMP>(b2.im, s2)));
+    cpx<T> q2 = rot90<T, INV>(mk(kmul<T, COMP>(b1.re, s2) - kmul<T, COMP>(b2.re, s1), kmul<T, COMP>(b1.im, s2) - kmul<T, COMP>(b2.im, s1)));
     v[0] = x0 + a1 + a2;
     v[1] = p1 + q1;
     v[4] = p1 - q1;
@@ -128,19 +128,19 @@ __host__ __device__ __forceinline__ void dft5(cpx<T>* v) {
     v[3] = p2 - q2;
 }
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool COMP = true>
 __host__ __device__ __forceinline__ void dft8(cpx<T>* v) {
     const double r = 0.70710678118654752440084436210485;
     cpx<T> e[4] = {v[0], v[2], v[4], v[6]};
     cpx<T> o[4] = {v[1], v[3], v[5], v[7]};
-    dft4<T, INV>(e);
-    dft4<T, INV>(o);
+    dft4<T, INV, COMP>(e);
+    dft4<T, INV, COMP>(o);
     // w8^k = exp(-+ 2 pi i k / 8), k = 1, 2, 3
-    cpx<T> o1 = INV ? mk(kmul(o[1].re - o[1].im, r), kmul(o[1].re + o[1].im, r))
-                    : mk(kmul(o[1].re + o[1].im, r), kmul(o[1].im - o[1].re, r));
+    cpx<T> o1 = INV ? mk(kmul<T, COMP>(o[1].re - o[1].im, r), kmul<T, COMP>(o[1].re + o[1].im, r))
+                    : mk(kmul<T, COMP>(o[1].re + o[1].im, r), kmul<T, COMP>(o[1].im - o[1].re, r));
     cpx<T> o2 = rot90<T, INV>(o[2]);
-    cpx<T> o3 = INV ? mk(-kmul(o[3].re + o[3].im, r), kmul(o[3].re - o[3].im, r))
-                    : mk(kmul(o[3].im - o[3].re, r), -kmul(o[3].re + o[3].im, r));
+    cpx<T> o3 = INV ? mk(-kmul<T, COMP>(o[3].re + o[3].im, r), kmul<T, COMP>(o[3].re - o[3].im, r))
+                    : mk(kmul<T, COMP>(o[3].im - o[3].re, r), -kmul<T, COMP>(o[3].re + o[3].im, r));
     v[0] = e[0] + o[0];
     v[4] = e[0] - o[0];
     v[1] = e[1] + o1;
@@ -153,19 +153,19 @@ __host__ __device__ __forceinline__ void dft8(cpx<T>* v) {
 
 // Radix 16 and 32 from two halves of half the size and the twiddles
 // exp(-+ 2 pi i k / R) = cos(2 pi k / R) -+ i sin(2 pi k / R).
-template <typename T, int R, bool INV>
+template <typename T, int R, bool INV, bool COMP>
 __host__ __device__ __forceinline__ void dft_halves(cpx<T>* v);
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool COMP = true>
 __host__ __device__ __forceinline__ void dft16(cpx<T>* v) {
-    dft_halves<T, 16, INV>(v);
+    dft_halves<T, 16, INV, COMP>(v);
 }
-template <typename T, bool INV>
+template <typename T, bool INV, bool COMP = true>
 __host__ __device__ __forceinline__ void dft32(cpx<T>* v) {
-    dft_halves<T, 32, INV>(v);
+    dft_halves<T, 32, INV, COMP>(v);
 }
 
-template <typename T, int R, bool INV>
+template <typename T, int R, bool INV, bool COMP>
 __host__ __device__ __forceinline__ void dft_halves(cpx<T>* v) {
     // cos(pi k / 16) and sin(pi k / 16), k = 0..16 (radix 32 uses every entry, radix 16 every second)
     const double C[17] = {1.0,
@@ -194,11 +194,11 @@ __host__ __device__ __forceinline__ void dft_halves(cpx<T>* v) {
         o[m] = v[2 * m + 1];
     }
     if constexpr (H == 8) {
-        dft8<T, INV>(e);
-        dft8<T, INV>(o);
+        dft8<T, INV, COMP>(e);
+        dft8<T, INV, COMP>(o);
     } else {
-        dft16<T, INV>(e);
-        dft16<T, INV>(o);
+        dft16<T, INV, COMP>(e);
+        dft16<T, INV, COMP>(o);
     }
 #pragma unroll
     for (int k = 0; k < H; ++k) {
@@ -212,22 +212,25 @@ __host__ __device__ __forceinline__ void dft_halves(cpx<T>* v) {
             const int m = k * step;
             const double c = C[m];
             const double sn = m <= 8 ? C[8 - m] : C[m - 8];
-            t = kcmul(o[k], c, INV ? sn : -sn);
+            t = kcmul<T, COMP>(o[k], c, INV ? sn : -sn);
         }
         v[k] = e[k] + t;
         v[k + H] = e[k] - t;
     }
 }
 
-template <typename T, int R, bool INV>
+// COMP (FP32 only): constants carried as high/low pairs.  Forward transforms,
+// whose spectrum feeds E_H, use it; inverse transforms, which only shape V_H,
+// may use plain constants.
+template <typename T, int R, bool INV, bool COMP = true>
 __host__ __device__ __forceinline__ void dft(cpx<T>* v) {
-    if constexpr (R == 2) dft2<T, INV>(v);
-    if constexpr (R == 3) dft3<T, INV>(v);
-    if constexpr (R == 4) dft4<T, INV>(v);
-    if constexpr (R == 5) dft5<T, INV>(v);
-    if constexpr (R == 8) dft8<T, INV>(v);
-    if constexpr (R == 16) dft16<T, INV>(v);
-    if constexpr (R == 32) dft32<T, INV>(v);
+    if constexpr (R == 2) dft2<T, INV, COMP>(v);
+    if constexpr (R == 3) dft3<T, INV, COMP>(v);
+    if constexpr (R == 4) dft4<T, INV, COMP>(v);
+    if constexpr (R == 5) dft5<T, INV, COMP>(v);
+    if constexpr (R == 8) dft8<T, INV, COMP>(v);
+    if constexpr (R == 16) dft16<T, INV, COMP>(v);
+    if constexpr (R == 32) dft32<T, INV, COMP>(v);
 }
 
 // ------------------------------------------------------------------ radix plans

@@ -2,6 +2,7 @@
 // library's translation units (not part of the public C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -75,6 +76,33 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
     return s;
 }
 
+// Sum over the block of values held as (s, e) pairs (value = s + e), reduced
+// inside each warp with error-free FP32 TwoSum steps and across warps in FP64.
+// FP64 throughput on GB300 is a small fraction of FP32, so per-thread FP64
+// shuffles would cost more than the kernel's own arithmetic.  Result valid in
+// thread 0; `red` holds one double per warp.  Contains __syncthreads().
+__device__ __forceinline__ double block_sum_comp(float s, float e, double* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+        const float e2 = __shfl_down_sync(0xffffffffu, e, o);
+        const float t = s + s2;
+        const float bb = t - s;
+        const float err = (s - (t - bb)) + (s2 - bb);
+        s = t;
+        e = e + e2 + err;
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = (double)s + (double)e;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+    return r;
+}
+__device__ __forceinline__ double block_sum_comp(double s, double e, double* red) {
+    return block_sum_double(s + e, red);
+}
+
 // Per-atom data prepared once per call (k_atom_prep): the cutoff box of the
 // atom in unwrapped grid indices and the offset of its first point, split in
 // a high and a low part so FP32 kernels can form d = (lo + m) h - X to full
@@ -144,7 +172,12 @@ struct Plan {
     // tiling
     int c_lines, b_cols, a_cols;
     mutable unsigned long long launches = 0;  // kernels launched (host-side count)
-    int use_fast = 0;  // bit 0: c passes, bit 1: b passes, bit 2: a pass use the specialised kernels
+    int use_fast = 0;
+    int var[3] = {0, 0, 0};  // kernel variant of the c, b and a passes (autotuned)
+    int sm_count = 0;
+    int* d_err = nullptr;     // device error word (bit 0: a bounded wait timed out)
+    bool tma_ok = false;      // tensor maps over W are valid
+    CUtensorMap tmap_b, tmap_a;  // bit 0: c passes, bit 1: b passes, bit 2: a pass use the specialised kernels
     size_t smem_c, smem_b, smem_a;
 };
 
@@ -179,6 +212,8 @@ void set_last_error(const char* msg);  // the message hartree_last_error() retur
 cudaError_t configure_poisson_kernels(const Plan& p);
 cudaError_t configure_fast_kernels(const Plan& p);
 int fast_pass_mask(const Plan& p);
+int fast_variants(const Plan& p, int kind);  // kind 0: c passes, 1: b passes, 2: a pass
+void prepare_tma(Plan& p);                   // encode the tensor maps of the TMA-streamed passes
 long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
 cudaError_t configure_atom_kernels(const Plan& p);
 

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_a_green(PoissonArgs<T> a) {
         sum = t;
         F[k1 * CA + col] = scale(v, inv * a.green_scale);
     }
-    const double bs = block_sum_double((double)sum - (double)comp, red);
+    const double bs = block_sum_comp(sum, -comp, red);
     if (threadIdx.x == 0) a.eh_partials[blockIdx.x] = bs;
     __syncthreads();
     cpx<T>* other = (F == A) ? B : A;

@@ -194,6 +194,20 @@ class HartreePlan:
         capi.check(capi.hartree_solve_pass(self.handle, int(pass_id), rho.data_ptr() if rho is not None else None,
                                            vh.data_ptr() if vh is not None else None, _stream_handle(self.device)))
 
+    def autotune(self):
+        """Time every kernel variant on this plan's workspace and keep the fastest; returns the picks."""
+        choice = (ctypes.c_int * 3)()
+        capi.check(capi.hartree_plan_autotune(self.handle, _stream_handle(self.device), choice))
+        return [int(v) for v in choice]
+
+    def set_variants(self, choice):
+        arr = (ctypes.c_int * 3)(*[int(v) for v in choice])
+        capi.check(capi.hartree_plan_set_variants(self.handle, arr))
+
+    def device_status(self):
+        """Raise HartreeError(TIMEOUT) if a bounded device wait gave up since the last check."""
+        capi.check(capi.hartree_plan_device_status(self.handle))
+
     @property
     def launch_count(self) -> int:
         return int(capi.hartree_plan_launch_count(self.handle))

@@ -269,3 +269,54 @@ def test_single_passes_reproduce_solve_density(precision):
     torch.cuda.synchronize()
     assert plan.launch_count - n0 == 5
     assert torch.equal(vh, vh_ref)
+
+
+@pytest.mark.parametrize(
+    "shape,precision", [((512, 256, 512), "fp32"), ((256, 512, 256), "fp32"), ((256, 512, 256), "fp64")]
+)
+def test_kernel_variants_give_identical_potential(shape, precision):
+    """Every compiled tile shape (and the TMA-streamed passes) computes the same V_H."""
+    import itertools
+
+    from paper_1209_4506_gb300 import capi
+
+    cell = (20.0, 12.0, 21.0)
+    rng = np.random.default_rng(17)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    rho = torch.tensor(rng.standard_normal(shape), dtype=dt, device="cuda")
+    v_ref, e_ref, _, _ = O.poisson(cell, rho.double().cpu().numpy())
+    plan = HartreePlan(shape, cell, 0.5, precision)
+    results = []
+    for choice in itertools.product(range(3), repeat=3):
+        try:
+            plan.set_variants(list(choice))
+        except capi.HartreeError:
+            continue
+        vh, eh = plan.solve_density(rho)
+        torch.cuda.synchronize()
+        results.append((choice, vh.clone(), eh.item()))
+    plan.device_status()
+    assert len(results) >= 8
+    for choice, vh, eh in results:
+        assert rel_l2(vh.double().cpu().numpy(), v_ref) <= TOL[precision]["v"], choice
+        assert torch.equal(vh, results[0][1]), choice
+        # E_H: same terms, different grouping (per-CTA partials, persistent CTAs sum across tiles)
+        assert abs(eh - results[0][2]) <= 1e-10 * abs(results[0][2]), choice
+    assert abs(results[0][2] - e_ref) <= WHITE_NOISE_E_TOL[precision] * abs(e_ref)
+    picks = plan.autotune()
+    plan.device_status()
+    assert all(0 <= p <= 2 for p in picks)
+    with pytest.raises(capi.HartreeError):
+        plan.set_variants([0, 0, 5])
+
+
+def test_autotune_cache_roundtrip(tmp_path):
+    from paper_1209_4506_gb300 import autotune
+
+    plan = HartreePlan((256, 256, 256), (20.0, 20.0, 20.0), 0.5, "fp32")
+    path = str(tmp_path / "cache.json")
+    first = autotune.tuned(plan, path)
+    again = autotune.tuned(plan, path)
+    assert first == again
+    import json
+    assert len(json.load(open(path))) == 1
