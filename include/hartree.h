@@ -216,6 +216,51 @@ int hartree_plan_device_status(hartree_plan plan);
 int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice);
 int hartree_plan_set_variants(hartree_plan plan, const int* choice);
 
+/* ---------------------------------------------------------------- batched cells */
+
+/*
+ * Many independent cells (different grids, cells and atom counts), each the
+ * operation of hartree_solve (Sec. 2.1 density, Poisson solve and E_H; the
+ * five transform passes of Sec. 3.2.4), in ONE persistent kernel launch.  All
+ * cells' work items (atom preparation, splat tiles, the tiles of each
+ * transform pass, the E_H sum) form one queue ordered stage by stage; resident
+ * CTAs take items from it and wait, with a bounded spin, until the previous
+ * stage of the same cell is complete.  Small cells no longer leave most SMs
+ * idle, and a batch costs one launch instead of about ten per cell.
+ *
+ * hartree_batch_create
+ *   descs        host [n_cells] descriptors; precision must be HARTREE_FP32
+ *                (each is validated as by hartree_plan_create; max_atoms is
+ *                replaced by atom_counts[c])
+ *   atom_counts  host [n_cells] atoms per cell, >= 0
+ *   out          host pointer receiving the batch.  Allocates one workspace
+ *                per cell plus the queue; HARTREE_ERR_OOM if it does not fit.
+ * hartree_batch_offsets
+ *   grid_off     host [n_cells + 1] out: first element of cell c in the
+ *                concatenated grid buffer (C order [N1][N2][N3] per cell);
+ *                grid_off[n_cells] is the total element count
+ *   atom_off     host [n_cells + 1] out: first atom of cell c in pos / q
+ * hartree_solve_batched
+ *   pos, q       device [sum atoms][3] / [sum atoms] doubles, cells concatenated
+ *   vh           device float [grid_off[n_cells]]: receives V_H of every cell
+ *                (also the density's scratch: the splat writes rho there first)
+ *   eh           device double [n_cells]: E_H of every cell
+ *   Enqueues two small memsets and one kernel; allocates nothing; can be
+ *   captured in a CUDA graph.  Results equal those of a plan solve of each
+ *   cell within the FP32 tolerance (the same per-element operations; only
+ *   the E_H partial sums are grouped differently).
+ * hartree_batch_device_status
+ *   Synchronises the device; HARTREE_ERR_TIMEOUT if a dependency wait gave
+ *   up since the last call (the results of that launch are incomplete), else
+ *   HARTREE_OK.  Clears the error word.
+ */
+int hartree_batch_create(const hartree_desc* descs, const int* atom_counts, int n_cells, hartree_batch* out);
+void hartree_batch_destroy(hartree_batch batch);
+int hartree_batch_offsets(hartree_batch batch, long long* grid_off, int* atom_off);
+int hartree_solve_batched(hartree_batch batch, const double* pos, const double* q, void* vh, double* eh,
+                          void* stream);
+int hartree_batch_device_status(hartree_batch batch);
+
 /* ---------------------------------------------------------------- no device allocation */
 
 /*

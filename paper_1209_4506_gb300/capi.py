@@ -44,6 +44,11 @@ EXPORTED = (
     "hartree_plan_autotune",
     "hartree_plan_set_variants",
     "hartree_plan_device_status",
+    "hartree_batch_create",
+    "hartree_batch_destroy",
+    "hartree_batch_offsets",
+    "hartree_solve_batched",
+    "hartree_batch_device_status",
     "hartree_status_string",
     "hartree_last_error",
 )
@@ -103,6 +108,12 @@ def lib():
             L.hartree_plan_autotune.argtypes = [_vp, _vp, _vp]
             L.hartree_plan_set_variants.argtypes = [_vp, _vp]
             L.hartree_plan_device_status.argtypes = [_vp]
+            L.hartree_batch_create.argtypes = [ctypes.POINTER(hartree_desc), _vp, _i, ctypes.POINTER(_vp)]
+            L.hartree_batch_destroy.argtypes = [_vp]
+            L.hartree_batch_destroy.restype = None
+            L.hartree_batch_offsets.argtypes = [_vp, _vp, _vp]
+            L.hartree_solve_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+            L.hartree_batch_device_status.argtypes = [_vp]
             L.hartree_status_string.argtypes = [_i]
             L.hartree_status_string.restype = ctypes.c_char_p
             L.hartree_last_error.argtypes = []
@@ -143,3 +154,8 @@ hartree_plan_set_variants = _call("hartree_plan_set_variants")
 hartree_plan_device_status = _call("hartree_plan_device_status")
 hartree_status_string = _call("hartree_status_string")
 hartree_last_error = _call("hartree_last_error")
+hartree_batch_create = _call("hartree_batch_create")
+hartree_batch_destroy = _call("hartree_batch_destroy")
+hartree_batch_offsets = _call("hartree_batch_offsets")
+hartree_solve_batched = _call("hartree_solve_batched")
+hartree_batch_device_status = _call("hartree_batch_device_status")

@@ -1,0 +1,261 @@
+// atoms_dev.cuh -- per-atom preparation and the density splat as device
+// functions, shared by the kernels of atoms.cu and the batched persistent
+// kernel of batch.cu.  See atoms.cu for the method.
+#pragma once
+
+#include "internal.cuh"
+
+namespace hartree {
+
+constexpr int TA = 16, TB = 8, TC = 32;  // splat tile (a, b, c)
+constexpr int kBatch = 32;               // atoms whose factors are staged at once
+constexpr int kPT = 12;                  // force gather: (b, c) points per thread held in registers
+
+__device__ __forceinline__ int imod(int x, int n) {
+    int r = x % n;
+    return r < 0 ? r + n : r;
+}
+
+// Does the index range [s, s + len) taken modulo n meet [t0, t0 + tn)?
+__device__ __forceinline__ bool range_hits(int s, int len, int t0, int tn, int n) {
+    if (len <= 0) return false;
+    if (len >= n) return true;
+    const int delta = imod(t0 - s, n);
+    return delta < len || delta + tn > n;
+}
+
+template <typename T>
+__device__ __forceinline__ void atom_prep_one(const AtomArgs<T>& a, int i) {
+    if (i >= a.n) return;
+    const double hs[3] = {a.h1, a.h2, a.h3};
+    const double Ls[3] = {a.L1, a.L2, a.L3};
+    AtomPrep<T> p;
+    for (int d = 0; d < 3; ++d) {
+        double X = a.pos[3 * i + d];
+        X -= Ls[d] * floor(X / Ls[d]);  // any image of the atom gives the same periodic sum
+        const double lo = ceil((X - a.rc) / hs[d]);
+        const double hi = floor((X + a.rc) / hs[d]);
+        p.lo[d] = (int)lo;
+        p.cnt[d] = hi >= lo ? min((int)(hi - lo) + 1, a.fb) : 0;
+        const double D0 = lo * hs[d] - X;
+        p.dh[d] = (T)D0;
+        p.dl[d] = (T)(D0 - (double)p.dh[d]);
+    }
+    const double qn = a.q[i] * a.norm;
+    p.qn = (T)qn;
+    p.ql = (T)(qn - (double)p.qn);
+    a.prep[i] = p;
+}
+
+// One thread per (atom, axis, run of kRun box points): fac / dfac computed in
+// FP64.  FP32 plans start each run with three exponentials and continue with
+// the exact ratio recurrence; FP64 plans evaluate every point directly.
+constexpr int kRun = 8;
+
+template <typename T>
+__device__ __forceinline__ void atom_factors_one(const AtomArgs<T>& a, long long t) {
+    const int runs = (a.fb + kRun - 1) / kRun;
+    if (t >= 3LL * a.n * runs) return;
+    const int i = (int)(t / (3 * runs));
+    const int rem = (int)(t - (long long)i * 3 * runs);
+    const int d = rem / runs, m0 = (rem - d * runs) * kRun;
+    const AtomPrep<T> p = a.prep[i];
+    const int cnt = p.cnt[d];
+    if (m0 >= cnt) return;
+    const int m1 = min(cnt, m0 + kRun);
+    const double h = d == 0 ? a.h1 : (d == 1 ? a.h2 : a.h3);
+    const double D0 = (double)p.dh[d] + (double)p.dl[d];  // lo h - X
+    T* f = a.fac + ((long long)i * 3 + d) * a.fb;
+    T* df = a.dfac + ((long long)i * 3 + d) * a.fb;
+    if constexpr (sizeof(T) == 8) {
+        for (int m = m0; m < m1; ++m) {
+            const double dm = fma((double)m, h, D0);
+            const double g = exp(-dm * dm * a.inv_s2);
+            f[m] = g;
+            df[m] = dm * g;
+        }
+    } else {
+        // exponent(m) = -(D0 + m h)^2 / s^2: successive ratios are exp(-(2 d_m h + h^2) / s^2)
+        const double ds = fma((double)m0, h, D0);
+        double g = exp(-ds * ds * a.inv_s2);
+        double r = exp(-(2.0 * ds * h + h * h) * a.inv_s2);
+        const double q = exp(-2.0 * h * h * a.inv_s2);
+        for (int m = m0; m < m1; ++m) {
+            const double dm = fma((double)m, h, D0);
+            f[m] = (T)g;
+            df[m] = (T)(dm * g);
+            g *= r;
+            r *= q;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void leaf_box_one(const AtomPrep<T>* __restrict__ prep, int n, int apl, int nleaves, int n1,
+                                             int n2, int n3, int* __restrict__ leaf, int l) {
+    if (l >= nleaves) return;
+    const int i0 = l * apl, i1 = min(n, i0 + apl);
+    const int ns[3] = {n1, n2, n3};
+    for (int d = 0; d < 3; ++d) {
+        const int lo0 = prep[i0].lo[d];
+        int s = lo0, e = lo0;
+        for (int i = i0; i < i1; ++i) {
+            int lo = prep[i].lo[d];
+            const int c = prep[i].cnt[d];
+            // shift by whole periods to the image nearest the leaf's first atom
+            const int diff = lo - lo0;
+            const int k = (int)floorf(((float)diff + 0.5f * ns[d]) / (float)ns[d]);
+            lo -= k * ns[d];
+            s = min(s, lo);
+            e = max(e, lo + c);
+        }
+        leaf[6 * l + d] = s;
+        leaf[6 * l + 3 + d] = min(e - s, ns[d]);
+    }
+}
+
+// Sum over the box points of one atom that land on grid index g (all images).
+template <typename T>
+__device__ __forceinline__ T image_sum(const T* __restrict__ f, int g, int lo, int cnt, int n) {
+    T s = T(0);
+    for (int m = imod(g - lo, n); m < cnt; m += n) s += f[m];
+    return s;
+}
+
+template <typename T>
+__device__ void splat_tile(const AtomArgs<T>& a, T* __restrict__ rho, int tiles_b, int tiles_c, int tile) {
+    __shared__ int leaf_list[kThreads];
+    __shared__ int cand[kThreads];
+    __shared__ int warp_cnt[kThreads / 32];
+    __shared__ int n_sel;
+    __shared__ __align__(16) T fa[kBatch][TA];
+    __shared__ T fb[kBatch][TB], fc[kBatch][TC];
+
+    const int ta = tile / (tiles_b * tiles_c);
+    const int tb = (tile / tiles_c) % tiles_b;
+    const int tc = tile % tiles_c;
+    const int a0 = ta * TA, b0 = tb * TB, c0 = tc * TC;
+    const int na = min(TA, a.n1 - a0), nb_ = min(TB, a.n2 - b0), nc_ = min(TC, a.n3 - c0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // ordered compaction of the threads whose flag is set; returns the count
+    auto compact = [&](bool flag, int value, int* out) -> int {
+        const unsigned bal = __ballot_sync(0xffffffffu, flag);
+        __syncthreads();  // earlier readers of warp_cnt / n_sel / out are done
+        if (lane == 0) warp_cnt[warp] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int s = 0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const int c = warp_cnt[w];
+                warp_cnt[w] = s;
+                s += c;
+            }
+            n_sel = s;
+        }
+        __syncthreads();
+        if (flag) out[warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u))] = value;
+        __syncthreads();
+        return n_sel;
+    };
+
+    T acc[TA];
+#pragma unroll
+    for (int i = 0; i < TA; ++i) acc[i] = T(0);
+
+    for (int lbase = 0; lbase < a.nleaves; lbase += kThreads) {
+        const int l = lbase + threadIdx.x;
+        bool hit = false;
+        if (l < a.nleaves) {
+            const int* bx = a.leaf + 6 * l;
+            hit = range_hits(bx[0], bx[3], a0, na, a.n1) && range_hits(bx[1], bx[4], b0, nb_, a.n2) &&
+                  range_hits(bx[2], bx[5], c0, nc_, a.n3);
+        }
+        const int nlf = compact(hit, l, leaf_list);
+        const int ncand_total = nlf * a.apl;
+        for (int cbase = 0; cbase < ncand_total; cbase += kThreads) {
+            const int c = cbase + threadIdx.x;
+            int atom = -1;
+            if (c < ncand_total) {
+                const int i = leaf_list[c / a.apl] * a.apl + (c % a.apl);
+                if (i < a.n) {
+                    const AtomPrep<T>& p = a.prep[i];
+                    if (range_hits(p.lo[0], p.cnt[0], a0, na, a.n1) && range_hits(p.lo[1], p.cnt[1], b0, nb_, a.n2) &&
+                        range_hits(p.lo[2], p.cnt[2], c0, nc_, a.n3))
+                        atom = i;
+                }
+            }
+            const int nc = compact(atom >= 0, atom, cand);
+            for (int bb = 0; bb < nc; bb += kBatch) {
+                const int nb = min(kBatch, nc - bb);
+                for (int e = threadIdx.x; e < nb * (TA + TB + TC); e += kThreads) {
+                    const int t = e / (TA + TB + TC), f = e - t * (TA + TB + TC);
+                    const int i = cand[bb + t];
+                    const AtomPrep<T>& p = a.prep[i];
+                    const T* F = a.fac + (long long)i * 3 * a.fb;
+                    if (f < TA) {
+                        fa[t][f] = image_sum(F, a0 + f, p.lo[0], p.cnt[0], a.n1);
+                    } else if (f < TA + TB) {
+                        fb[t][f - TA] = image_sum(F + a.fb, b0 + f - TA, p.lo[1], p.cnt[1], a.n2);
+                    } else {
+                        const int k = f - TA - TB;
+                        const T sc = image_sum(F + 2 * a.fb, c0 + k, p.lo[2], p.cnt[2], a.n3);
+                        fc[t][k] = p.qn * sc + p.ql * sc;
+                    }
+                }
+                __syncthreads();
+                for (int t = 0; t < nb; ++t) {
+                    const T s = fb[t][warp] * fc[t][lane];
+#pragma unroll
+                    for (int i = 0; i < TA; ++i) acc[i] += fa[t][i] * s;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    const int b = b0 + warp, c = c0 + lane;
+    if (b < a.n2 && c < a.n3) {
+#pragma unroll
+        for (int i = 0; i < TA; ++i) {
+            const int ia = a0 + i;
+            if (ia < a.n1) rho[((long long)ia * a.n2 + b) * a.n3 + c] = acc[i];
+        }
+    }
+}
+
+template <typename T>
+inline AtomArgs<T> make_atom_args(const Plan& p, const double* pos, const double* q, int n) {
+    AtomArgs<T> a;
+    a.n1 = p.n[0];
+    a.n2 = p.n[1];
+    a.n3 = p.n[2];
+    a.h1 = p.h[0];
+    a.h2 = p.h[1];
+    a.h3 = p.h[2];
+    for (int d = 0; d < 3; ++d) {
+        a.hh[d] = (T)p.h[d];
+        a.hl[d] = (T)(p.h[d] - (double)a.hh[d]);
+    }
+    a.L1 = p.L[0];
+    a.L2 = p.L[1];
+    a.L3 = p.L[2];
+    a.rc = p.rc;
+    a.inv_s2 = 1.0 / (p.sigma * p.sigma);
+    a.is2h = (T)a.inv_s2;
+    a.is2l = (T)(a.inv_s2 - (double)a.is2h);
+    a.norm = pow(3.14159265358979323846 * p.sigma * p.sigma, -1.5);
+    a.dV = p.dV;
+    a.pos = pos;
+    a.q = q;
+    a.n = n;
+    a.apl = p.apl;
+    a.nleaves = (n + p.apl - 1) / p.apl;
+    a.prep = static_cast<AtomPrep<T>*>(p.atom_prep);
+    a.fac = static_cast<T*>(p.atom_fac);
+    a.dfac = static_cast<T*>(p.atom_dfac);
+    a.fb = p.box_max;
+    a.leaf = p.leaf_box;
+    return a;
+}
+
+}  // namespace hartree

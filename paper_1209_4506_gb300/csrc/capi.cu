@@ -11,10 +11,6 @@
 
 using namespace hartree;
 
-struct hartree_plan_s {
-    Plan p;
-};
-
 namespace {
 
 thread_local std::string g_last_error;

@@ -252,11 +252,28 @@ struct SmemTile {
     __device__ __forceinline__ void st_(int col, int n, cpx<T> v) const { p[n * ld + col] = v; }
 };
 
-template <typename T>
+// Global load; CG = true bypasses L1 (ld.global.cg), needed when the data was
+// written by another CTA of the same launch (L1 is not coherent across SMs).
+template <bool CG, typename T>
+__device__ __forceinline__ cpx<T> gload(const cpx<T>* p) {
+    if constexpr (CG) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+            return mk(v.x, v.y);
+        } else {
+            const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+            return mk(v.x, v.y);
+        }
+    } else {
+        return *p;
+    }
+}
+
+template <typename T, bool CG = false>
 struct GlobalTile {
     cpx<T>* p;
     long long sn;  // element stride along the line
-    __device__ __forceinline__ cpx<T> ld_(int col, int n) const { return p[(long long)n * sn + col]; }
+    __device__ __forceinline__ cpx<T> ld_(int col, int n) const { return gload<CG>(p + (long long)n * sn + col); }
     __device__ __forceinline__ void st_(int col, int n, cpx<T> v) const { p[(long long)n * sn + col] = v; }
 };
 

@@ -114,6 +114,8 @@ struct AtomPrep {
     T dh[3];     // lo h - X, rounded to T
     T dl[3];     // (lo h - X) - dh (zero for FP64)
     T qn;        // q (pi s^2)^(-3/2), formed in FP64 and rounded once
+    T ql;        // its rounding remainder (q norm - qn): one shared rounding of every point of
+                 // the atom would otherwise bias E_H by twice its relative size
 };
 
 // Arguments of the splat and the force gather.
@@ -218,3 +220,8 @@ long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, c
 cudaError_t configure_atom_kernels(const Plan& p);
 
 }  // namespace hartree
+
+// The opaque handle of the C ABI.
+struct hartree_plan_s {
+    hartree::Plan p;
+};

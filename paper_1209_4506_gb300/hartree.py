@@ -222,3 +222,90 @@ class HartreePlan:
         capi.check(capi.hartree_step_host(self.handle, pos.ctypes.data, q.ctypes.data, n, eh.ctypes.data,
                                           f.ctypes.data if forces else None, _stream_handle(self.device)))
         return float(eh[0]), f
+
+
+class HartreeBatch:
+    """Many FP32 cells (each its own grid, cell, width and atom count) solved in one persistent launch.
+
+    cells: sequence of (n, cell, sigma, n_atoms).  Positions and charges of all
+    cells are concatenated in cell order; V_H of all cells is one flat float32
+    buffer, cell c occupying grid_off[c]:grid_off[c + 1] in C order.
+    """
+
+    def __init__(self, cells, cutoff_sigmas: float = 0.0, atoms_per_leaf: int = 0, device=None):
+        torch = _torch()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+        cells = list(cells)
+        self.n_cells = len(cells)
+        descs = (capi.hartree_desc * max(self.n_cells, 1))()
+        counts = np.zeros(max(self.n_cells, 1), dtype=np.int32)
+        self.shapes = []
+        for c, (n, cell, sigma, nat) in enumerate(cells):
+            d = descs[c]
+            for i in range(3):
+                d.n[i] = int(n[i])
+                d.cell[i] = float(cell[i])
+            d.sigma = float(sigma)
+            d.cutoff_sigmas = float(cutoff_sigmas)
+            d.precision = capi.HARTREE_FP32
+            d.atoms_per_leaf = int(atoms_per_leaf)
+            d.max_atoms = 0
+            d.flags = 0
+            counts[c] = int(nat)
+            self.shapes.append(tuple(int(v) for v in n))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            capi.check(capi.hartree_batch_create(descs, counts.ctypes.data, self.n_cells, ctypes.byref(h)))
+        self._h = h
+        go = np.zeros(self.n_cells + 1, dtype=np.int64)
+        ao = np.zeros(self.n_cells + 1, dtype=np.int32)
+        capi.check(capi.hartree_batch_offsets(self.handle, go.ctypes.data, ao.ctypes.data))
+        self.grid_off = go
+        self.atom_off = ao
+
+    @property
+    def handle(self) -> int:
+        if self._h is None:
+            raise RuntimeError("batch is closed")
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            capi.hartree_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, pos, q, vh=None, eh=None):
+        """V_H (flat float32 [grid_off[-1]]) and E_H (float64 [n_cells]) of every cell."""
+        torch = _torch()
+        n_at = int(self.atom_off[-1])
+        if pos.dtype != torch.float64 or q.dtype != torch.float64 or pos.device != self.device or q.device != self.device:
+            raise ValueError("pos and q must be float64 tensors on the batch's device")
+        pos = pos.contiguous().reshape(-1, 3)
+        q = q.contiguous().reshape(-1)
+        if pos.shape[0] != n_at or q.shape[0] != n_at:
+            raise ValueError(f"expected {n_at} atoms in total")
+        total = int(self.grid_off[-1])
+        if vh is None:
+            vh = torch.empty(total, dtype=torch.float32, device=self.device)
+        elif vh.dtype != torch.float32 or vh.numel() != total or not vh.is_contiguous() or vh.device != self.device:
+            raise ValueError(f"vh: expected a contiguous float32 tensor of {total} elements")
+        if eh is None:
+            eh = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        elif eh.dtype != torch.float64 or eh.numel() != self.n_cells or eh.device != self.device:
+            raise ValueError(f"eh: expected a float64 tensor of {self.n_cells} elements")
+        capi.check(capi.hartree_solve_batched(self.handle, pos.data_ptr(), q.data_ptr(), vh.data_ptr(), eh.data_ptr(),
+                                              _stream_handle(self.device)))
+        return vh, eh
+
+    def cell_view(self, vh, c):
+        """The grid of cell c inside the flat buffer, shaped [N1][N2][N3]."""
+        return vh[int(self.grid_off[c]):int(self.grid_off[c + 1])].view(self.shapes[c])
+
+    def device_status(self):
+        capi.check(capi.hartree_batch_device_status(self.handle))

@@ -108,7 +108,7 @@ def jitter(rng: np.random.Generator, pos: np.ndarray, amount: float, cell) -> np
 def centred_uniform_charges(rng: np.random.Generator, n: int) -> np.ndarray:
     """q ~ U(-1, 1), then shifted by its mean so the cell is neutral."""
     q = rng.uniform(-1.0, 1.0, size=n)
-    return q - q.mean()
+    return q - q.mean() if n > 0 else q
 
 
 def smooth235(x: float, even: bool = True) -> int:

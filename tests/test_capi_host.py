@@ -162,3 +162,31 @@ def test_library_bisection_rejects_bad_input():
         atoms_reorder(pos, 2)
     with pytest.raises(capi.HartreeError):
         atoms_reorder(np.zeros((4, 3)), 0)
+
+
+def _fp32_desc(prec=None):
+    d = capi.hartree_desc()
+    for i in range(3):
+        d.n[i] = 48
+        d.cell[i] = 8.0
+    d.sigma = 0.6
+    d.precision = capi.HARTREE_FP32 if prec is None else prec
+    return d
+
+
+def test_batch_create_rejects_before_any_device_work():
+    h = ctypes.c_void_p()
+    descs = (capi.hartree_desc * 3)(_fp32_desc(), _fp32_desc(), _fp32_desc(capi.HARTREE_FP64))
+    counts = np.array([4, 0, 7], dtype=np.int32)
+    # the third cell is FP64: rejected before the first cell's workspace is created
+    assert capi.hartree_batch_create(descs, counts.ctypes.data, 3, ctypes.byref(h)) == capi.HARTREE_ERR_INVALID
+    assert h.value is None
+    descs[2] = _fp32_desc()
+    bad = np.array([4, -1, 7], dtype=np.int32)
+    assert capi.hartree_batch_create(descs, bad.ctypes.data, 3, ctypes.byref(h)) == capi.HARTREE_ERR_INVALID
+    assert capi.hartree_batch_create(descs, counts.ctypes.data, 0, ctypes.byref(h)) == capi.HARTREE_ERR_INVALID
+    assert capi.hartree_batch_create(None, None, 1, None) == capi.HARTREE_ERR_INVALID
+    assert capi.hartree_solve_batched(None, None, None, None, None, None) == capi.HARTREE_ERR_INVALID
+    assert capi.hartree_batch_offsets(None, None, None) == capi.HARTREE_ERR_INVALID
+    assert capi.hartree_batch_device_status(None) == capi.HARTREE_ERR_INVALID
+    capi.hartree_batch_destroy(None)
