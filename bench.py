@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="diamond512", choices=["diamond512", "diamond256"],
+                    help="diamond256: the 4x4x4 cell on 256^3 (same density and sigma), for small profiler captures")
+    ap.add_argument("--skip-side", action="store_true", help="skip the e2e, adjoint and batched measurements")
     return ap.parse_args()
 
 
@@ -165,6 +168,149 @@ def kernel_traffic(name):
         return None
 
 
+def time_events(fn, reps, stream, warm=3):
+    """Average device milliseconds of fn() over reps calls (CUDA events on `stream`)."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def graph_of(fn, stream):
+    """Capture fn() (after one eager call on a side stream) into a CUDA graph."""
+    import torch
+
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        fn()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    return g
+
+
+def batched_section(dev, stream, reps):
+    """64 uneven FP32 cells: one persistent launch vs 64 plan solves, both replayed from CUDA graphs."""
+    import numpy as np
+    import torch
+
+    from paper_1209_4506_gb300 import synth
+    from paper_1209_4506_gb300.hartree import HartreeBatch, HartreePlan
+
+    cells = synth.config4()
+    pts = sum(int(np.prod(S.n)) for S in cells)
+    B = HartreeBatch([(S.n, S.cell, S.sigma, S.n_atoms) for S in cells])
+    pos = torch.tensor(np.concatenate([S.pos for S in cells]).reshape(-1, 3), device=dev)
+    q = torch.tensor(np.concatenate([S.q for S in cells]), device=dev)
+    vh = torch.empty(int(B.grid_off[-1]), dtype=torch.float32, device=dev)
+    eh = torch.empty(len(cells), dtype=torch.float64, device=dev)
+    gB = graph_of(lambda: B.solve(pos, q, vh, eh), stream)
+    t_b = time_events(gB.replay, reps, stream)
+    B.device_status()
+    eh_b = eh.clone()
+    plans, args = [], []
+    for S in cells:
+        P = HartreePlan(S.n, S.cell, S.sigma, "fp32", max_atoms=max(S.n_atoms, 1))
+        plans.append(P)
+        args.append((torch.tensor(S.pos, device=dev), torch.tensor(S.q, device=dev),
+                     torch.empty(S.n, dtype=torch.float32, device=dev), torch.empty((), dtype=torch.float64, device=dev)))
+
+    def plain():
+        for P, (p_, q_, v_, e_) in zip(plans, args):
+            P.solve(p_, q_, vh=v_, eh=e_)
+
+    t_p_eager = time_events(plain, max(3, reps // 4), stream)
+    gP = graph_of(plain, stream)
+    t_p = time_events(gP.replay, reps, stream)
+    eh_p = torch.stack([a[3] for a in args])
+    max_rel = float(((eh_b - eh_p).abs() / eh_p.abs()).max().item())
+    y = 40.0 * pts
+    out = {"cells": len(cells), "grid_points": pts, "atoms": int(B.atom_off[-1]), "launches_per_solve": 1,
+           "batched_ms": t_b, "batched_gbs": y / (t_b * 1e-3) / 1e9,
+           "plain_ms": t_p, "plain_gbs": y / (t_p * 1e-3) / 1e9, "plain_eager_ms": t_p_eager,
+           "speedup_vs_plain_graph": t_p / t_b, "eh_max_rel_diff_vs_plain": max_rel,
+           "form": "CUDA graph replay of hartree_solve_batched vs of 64 hartree_solve calls (splat + 5 passes + E_H)"}
+    for P in plans:
+        P.close()
+    B.close()
+    return out
+
+
+def adjoint_section(plan, pos, q, rho, vh, stream, reps, plain_solve_ms):
+    """Forward + backward through the autograd wrappers at the bench's grid, beside the plain solve."""
+    import torch
+
+    from paper_1209_4506_gb300.autograd import hartree_energy, hartree_energy_atoms
+
+    pos_g = pos.clone().requires_grad_(True)
+    q_g = q.clone().requires_grad_(True)
+
+    def atoms(store):
+        def f():
+            pos_g.grad = None
+            q_g.grad = None
+            e = hartree_energy_atoms(pos_g, q_g, plan, store_potential=store)
+            e.backward()
+        return f
+
+    plan.splat(pos, q, rho)
+    rho_g = rho.clone().requires_grad_(True)
+
+    def dens():
+        rho_g.grad = None
+        hartree_energy(rho_g, plan).backward()
+
+    t_rec = time_events(atoms(False), reps, stream)
+    t_sto = time_events(atoms(True), reps, stream)
+    t_den = time_events(dens, reps, stream)
+    return {"atoms_recompute_ms": t_rec, "atoms_stored_potential_ms": t_sto, "density_ms": t_den,
+            "plain_solve_ms": plain_solve_ms,
+            "form": "torch.autograd forward + backward: E_H(pos, q) -> (-F, phi), recomputing V_H in the backward "
+                    "(or keeping it); E_H(rho) -> V_H dV (backward = one more solve)"}
+
+
+def side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrier, ybytes, plain_solve_ms, dev):
+    """e2e through the C ABI with host buffers, the adjoint forms and the batched form."""
+    import torch
+    import torch.distributed as dist
+
+    # end to end: pinned host buffers in, host results out, copies and read-back inside the timed region
+    pos_pin = torch.tensor(pos_h).pin_memory()
+    q_pin = torch.tensor(q_h).pin_memory()
+    for _ in range(3):
+        plan.step_host(pos_pin.numpy(), q_pin.numpy())
+    n_e2e = max(10, min(args.steps, 100))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        plan.step_host(pos_pin.numpy(), q_pin.numpy())
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": world * ybytes * n_e2e / t_e2e / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": int(pos_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(8 + pos_h.nbytes),
+           "ms_per_step": 1e3 * t_e2e / n_e2e, "api": "hartree_step_host"}
+    side_reps = max(5, min(args.steps, 50))
+    adjoint = adjoint_section(plan, pos, q, rho, vh, stream, side_reps, plain_solve_ms)
+    batched = batched_section(dev, stream, side_reps)
+    return e2e, adjoint, batched
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -189,13 +335,19 @@ def main():
         if world > 1:
             dist.barrier()
 
-    S = synth.config3a()
+    if args.workload == "diamond512":
+        S = synth.config3a()
+        wl_text = "diamond 8x8x8 supercell, 4096 Gaussian charges (sigma 0.5 Bohr, cutoff 5 sigma), 512^3 grid"
+    else:
+        S = synth.config5()
+        wl_text = "diamond 4x4x4 supercell, 512 Gaussian charges (sigma 0.5 Bohr, cutoff 5 sigma), 256^3 grid"
     apl = 16
     t0 = time.perf_counter()
     perm, _ = atoms_reorder(S.pos, (S.n_atoms + apl - 1) // apl)
     reorder_ms = 1e3 * (time.perf_counter() - t0)
     pos_h, q_h = S.pos[perm], S.q[perm]
     plan = HartreePlan(S.n, S.cell, S.sigma, "fp32", atoms_per_leaf=apl, max_atoms=S.n_atoms)
+    variants = plan.autotune()
     pos = torch.tensor(pos_h, device=dev)
     q = torch.tensor(q_h, device=dev)
     vh = torch.empty(S.n, dtype=torch.float32, device=dev)
@@ -220,10 +372,12 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
@@ -262,10 +416,9 @@ def main():
     alg = {"splat": 4.0 * ntot, "pass0_c_r2c": 4.0 * ntot + half, "pass1_b_fwd": 2 * half,
            "pass2_a_green": 2 * half, "pass3_b_inv": 2 * half, "pass4_c_c2r": half + 4.0 * ntot,
            "forces": 4.0 * ntot}
-    kernel_names = {"splat": "k_splat<float>", "pass0_c_r2c": "k_r2c_fast<float,16,256,16,16,1>",
-                    "pass1_b_fwd": "k_col_fast<float,16,512,8,8,8,0>", "pass2_a_green": "k_col_fast<float,16,512,8,8,8,2>",
-                    "pass3_b_inv": "k_col_fast<float,16,512,8,8,8,1>", "pass4_c_c2r": "k_c2r_fast<float,16,256,16,16,1>",
-                    "forces": "k_forces<float>"}
+    kernel_names = {"splat": "k_splat<float>", "pass0_c_r2c": "k_r2c_fast", "pass1_b_fwd": "k_col_fast/k_col_tma MODE 0",
+                    "pass2_a_green": "k_col_fast/k_col_tma MODE 2", "pass3_b_inv": "k_col_fast/k_col_tma MODE 1",
+                    "pass4_c_c2r": "k_c2r_fast", "forces": "k_forces<float>"}
     dom = max(names, key=lambda k: kernels_ms[k])
     pk, src = peaks()
     achieved = alg[dom] / (kernels_ms[dom] * 1e-3) / 1e9
@@ -273,25 +426,14 @@ def main():
                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": kernel_traffic(kernel_names[dom]),
                 "algorithmic_bytes": alg[dom], "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
                 if src == "measured" else "fallback 6.8 TB/s"}
+    solve_roofline = {"bound": "hbm", "achieved": ybytes / (solve_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                      "unit": "GB/s", "frac": ybytes / (solve_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                      "note": "five Poisson passes, 40 N_tot algorithmic bytes"}
 
-    # end to end through the C ABI with host buffers (pinned), copies and read-back inside the timed region
-    pos_pin = torch.tensor(pos_h).pin_memory()
-    q_pin = torch.tensor(q_h).pin_memory()
-    for _ in range(3):
-        plan.step_host(pos_pin.numpy(), q_pin.numpy())
-    n_e2e = max(10, min(args.steps, 100))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(n_e2e):
-        plan.step_host(pos_pin.numpy(), q_pin.numpy())
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = {"value": world * ybytes * n_e2e / t_e2e / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": int(pos_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(8 + pos_h.nbytes),
-           "ms_per_step": 1e3 * t_e2e / n_e2e, "api": "hartree_step_host"}
+    e2e = adjoint = batched = None
+    if not args.skip_side:
+        e2e, adjoint, batched = side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrier, ybytes,
+                                              solve_ms + kernels_ms["splat"], dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -306,14 +448,16 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "diamond 8x8x8 supercell, 4096 Gaussian charges (sigma 0.5 Bohr, cutoff 5 sigma), "
-                                   "512^3 grid, FP32: splat + Poisson + E_H + forces",
+            "config": {"workload": wl_text + ", FP32: splat + Poisson + E_H + forces",
                        "grid": list(S.n), "atoms": S.n_atoms, "yardstick_bytes_per_step": ybytes,
-                       "l2": "inputs larger than L2 (each grid array 0.5 GB)",
-                       "parallelism": f"replicas x{world}"},
+                       "l2": "inputs larger than L2 (each grid array 0.5 GB)" if S.n[0] == 512 else
+                             "working set larger than L2 (three 64 MB grid arrays); profiling case",
+                       "parallelism": f"replicas x{world}", "variants": variants},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "solve_ms": solve_ms, "solve_gbs": ybytes / (solve_ms * 1e-3) / 1e9,
-            "kernels_ms": kernels_ms, "reorder_ms": reorder_ms, "eh": float(eh.item()),
+            "solve_points_per_s": ntot / (solve_ms * 1e-3), "solve_roofline": solve_roofline,
+            "kernels_ms": kernels_ms, "batched": batched, "adjoint": adjoint, "reorder_ms": reorder_ms,
+            "eh": float(eh.item()),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -31,7 +31,10 @@
 //   sum_r V f(x) f(y) f(z) -> phi_i = dE_H/dq_i,   sum_r V f'(x) f(y) f(z) ... -> F_i
 // use compensated working-precision accumulators and one FP64 block
 // reduction.  Per (atom, slab) partials are reduced in a fixed order.
+#include <algorithm>
+
 #include "atoms_dev.cuh"
+#include "tma.cuh"
 
 namespace hartree {
 
@@ -57,6 +60,155 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_splat(AtomArgs<T> a, T* __restrict__ rho, int tiles_b, int tiles_c) {
     splat_tile(a, rho, tiles_b, tiles_c, blockIdx.x);
 }
+// ---------------------------------------------------------------- tile binning
+// The tiles along one axis that hold at least one wrapped index of the box
+// [lo, lo + cnt): count of them, and tile(k) for k < count.
+struct AxisTiles {
+    int start, c1, count;
+    __device__ __forceinline__ int tile(int k) const { return k < c1 ? start + k : k - c1; }
+};
+
+__device__ __forceinline__ AxisTiles axis_tiles(int lo, int cnt, int n, int T, int nT) {
+    if (cnt <= 0) return {0, 0, 0};
+    if (cnt >= n) return {0, nT, nT};
+    const int s = imod(lo, n), e = s + cnt;
+    const int t0 = s / T;
+    if (e <= n) {
+        const int c = (e - 1) / T - t0 + 1;
+        return {t0, c, c};
+    }
+    const int t2 = (e - n - 1) / T;  // last tile of the segment wrapped to the start
+    if (t2 >= t0) return {0, nT, nT};  // both segments meet: every tile
+    return {t0, nT - t0, nT - t0 + t2 + 1};
+}
+
+// One warp per atom enumerates the tiles its box reaches.  FILL = false counts
+// atoms per tile; FILL = true appends the atom to each tile's list (order fixed
+// later by the splat, which sorts each list).
+template <typename T, bool FILL>
+__global__ void k_bin(AtomArgs<T> a, int tA, int tB, int tC, int* __restrict__ count, const int* __restrict__ off,
+                      int* __restrict__ cursor, int* __restrict__ list) {
+    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= a.n) return;
+    const AtomPrep<T>& p = a.prep[i];
+    const AxisTiles ra = axis_tiles(p.lo[0], p.cnt[0], a.n1, TA, tA);
+    const AxisTiles rb = axis_tiles(p.lo[1], p.cnt[1], a.n2, TB, tB);
+    const AxisTiles rc = axis_tiles(p.lo[2], p.cnt[2], a.n3, TC, tC);
+    const int nbc = rb.count * rc.count;
+    const int tot = ra.count * nbc;
+    for (int k = lane; k < tot; k += 32) {
+        const int ka = k / nbc, r = k - ka * nbc, kb = r / rc.count, kc = r - kb * rc.count;
+        const int tile = (ra.tile(ka) * tB + rb.tile(kb)) * tC + rc.tile(kc);
+        if (FILL)
+            list[off[tile] + atomicAdd(cursor + tile, 1)] = i;
+        else
+            atomicAdd(count + tile, 1);
+    }
+}
+
+// Exclusive prefix sum of the per-tile counts (one CTA of 1024 threads, in
+// chunks of 4096 counts with a running carry); also clears the fill cursors.
+// off[n_tiles] is the total.
+__global__ void __launch_bounds__(1024) k_bin_scan(const int* __restrict__ count, int n_tiles, int* __restrict__ off,
+                                                   int* __restrict__ cursor) {
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int carry = 0;
+    for (int base = 0; base < n_tiles; base += 4096) {
+        const int t0 = base + 4 * threadIdx.x;
+        int v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = t0 + k < n_tiles ? count[t0 + k] : 0;
+        const int sum = v[0] + v[1] + v[2] + v[3];
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_tot[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int x = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            warp_tot[lane] = x;  // inclusive over warps
+        }
+        __syncthreads();
+        int run = carry + incl - sum + (w > 0 ? warp_tot[w - 1] : 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (t0 + k < n_tiles) {
+                off[t0 + k] = run;
+                cursor[t0 + k] = 0;
+                run += v[k];
+            }
+        carry += warp_tot[31];
+        __syncthreads();  // warp_tot is rewritten by the next chunk
+    }
+    if (threadIdx.x == 0) off[n_tiles] = carry;
+}
+
+constexpr int kBinCap = 1024;  // longest tile list the binned splat sorts in shared memory
+
+// Splat of one tile from its bin: the list is sorted by atom index in shared
+// memory (a rank sort; indices in a list are distinct), so the summation order
+// is the same as that of the leaf-selecting splat, then factors are staged in
+// batches and accumulated as there.  Longer lists take the leaf-selecting path.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_splat_binned(AtomArgs<T> a, T* __restrict__ rho, int tiles_b,
+                                                           int tiles_c, const int* __restrict__ count,
+                                                           const int* __restrict__ off,
+                                                           const int* __restrict__ list) {
+    __shared__ int ids[kBinCap];
+    __shared__ int sorted[kBinCap];
+    __shared__ __align__(16) T fa[kBatch][TA];
+    __shared__ T fb[kBatch][TB], fc[kBatch][TC];
+    const int tile = blockIdx.x;
+    const int L = count[tile];
+    if (L > kBinCap) {
+        splat_tile(a, rho, tiles_b, tiles_c, tile);
+        return;
+    }
+    const int base = off[tile];
+    for (int e = threadIdx.x; e < L; e += kThreads) ids[e] = list[base + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < L; e += kThreads) {
+        const int v = ids[e];
+        int r = 0;
+        for (int f = 0; f < L; ++f) r += ids[f] < v;
+        sorted[r] = v;
+    }
+    const int ta = tile / (tiles_b * tiles_c);
+    const int tb = (tile / tiles_c) % tiles_b;
+    const int tc = tile % tiles_c;
+    const int a0 = ta * TA, b0 = tb * TB, c0 = tc * TC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T acc[TA];
+#pragma unroll
+    for (int i = 0; i < TA; ++i) acc[i] = T(0);
+    for (int bb = 0; bb < L; bb += kBatch) {
+        const int nb = min(kBatch, L - bb);
+        __syncthreads();  // sorted[] complete / previous batch consumed
+        stage_factors(a, sorted + bb, nb, a0, b0, c0, fa, fb, fc);
+        __syncthreads();
+        for (int t = 0; t < nb; ++t) {
+            const T s = fb[t][warp] * fc[t][lane];
+#pragma unroll
+            for (int i = 0; i < TA; ++i) acc[i] += fa[t][i] * s;
+        }
+    }
+    const int b = b0 + warp, c = c0 + lane;
+    if (b < a.n2 && c < a.n3) {
+#pragma unroll
+        for (int i = 0; i < TA; ++i) {
+            const int ia = a0 + i;
+            if (ia < a.n1) rho[((long long)ia * a.n2 + b) * a.n3 + c] = acc[i];
+        }
+    }
+}
 
 // ---------------------------------------------------------------- forces
 template <typename T>
@@ -67,80 +219,202 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
     s = t;
 }
 
-// Dynamic shared memory: fac[3][fb], dfac[3][fb], wrapped grid index[3][fb].
+// Vector of VW consecutive values along c, loaded with one 8- or 16-byte access.
+template <typename T, int VW>
+struct VecLoad;
+template <>
+struct VecLoad<float, 4> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+    }
+};
+template <>
+struct VecLoad<float, 2> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        const float2 x = __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = x.x, v[1] = x.y;
+    }
+};
 template <typename T>
+struct VecLoad<T, 1> {
+    static __device__ __forceinline__ void ld(const T* p, T* v) { v[0] = __ldg(p); }
+};
+template <>
+struct VecLoad<double, 2> {
+    static __device__ __forceinline__ void ld(const double* p, double* v) {
+        const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+        v[0] = x.x, v[1] = x.y;
+    }
+};
+
+constexpr int kDepth = 4;  // slices of V in flight per thread in the force gather
+
+// Offset (elements of T) of the cp.async ring after the six weight rows of length ld, 16-byte aligned.
+template <typename T>
+__host__ __device__ __forceinline__ int ring_offset(int ld) {
+    return (int)(((size_t)6 * ld * sizeof(T) + 15) / 16 * 16 / sizeof(T));
+}
+
+// Force gather of one atom (or a slab of its a range) per CTA.
+//
+// V is periodic, so sum_m fac[m] V[(lo + m) mod n] = sum_t w[t] V[(lo + t) mod n]
+// over the min(cnt, n) distinct wrapped indices t, with the image-summed weight
+// w[t] = sum_{m = t (mod n), m < cnt} fac[m] (likewise for dfac).  Shared memory
+// holds these weights for the three axes; the c axis is laid out in slots of VW
+// starting at the VW-aligned wrapped index below the box, zero outside it, so
+// each (b row, c group) pair is one aligned vector load.  Per a slice a thread
+// contracts its KP pairs: r0 = sum_e V_e wc_e, r1 = sum_e V_e dwc_e, then
+// p0 += wb r0, py += dwb r0, pz += wb r1; slices are combined with wa / dwa in
+// compensated sums.  The gather is bound by loads in flight, not by
+// arithmetic: each thread keeps kDepth slices of its pairs in flight with
+// cp.async copies into a private ring in shared memory.
+template <typename T, int VW, int KP>
 __global__ void __launch_bounds__(kThreads) k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs,
                                                      double* __restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int fb = a.fb;
-    T* f0 = reinterpret_cast<T*>(smem_raw);
-    T* f1 = f0 + 3 * fb;
-    int* gix = reinterpret_cast<int*>(f1 + 3 * fb);
+    const int ld = fb + 8;
+    T* wf = reinterpret_cast<T*>(smem_raw);  // [3][ld] image-summed fac (c axis: per slot)
+    T* wd = wf + 3 * ld;                     // [3][ld] image-summed dfac
     __shared__ double red[4][kThreads / 32];
     const int atom = blockIdx.x / slabs, slab = blockIdx.x - atom * slabs;
     const AtomPrep<T> p = a.prep[atom];
-    const int ns[3] = {a.n1, a.n2, a.n3};
+    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+    int nw[3], st[3];
+    nw[0] = min(p.cnt[0], n1), nw[1] = min(p.cnt[1], n2), nw[2] = min(p.cnt[2], n3);
+    st[0] = imod(p.lo[0], n1), st[1] = imod(p.lo[1], n2), st[2] = imod(p.lo[2], n3);
+    const int lead = st[2] % VW;  // VW divides n3
+    const int cst = st[2] - lead;
+    const int nslot = (lead + nw[2] + VW - 1) / VW * VW;
+    const int ng = nslot / VW;
     const T* F = a.fac + (long long)atom * 3 * fb;
     const T* DF = a.dfac + (long long)atom * 3 * fb;
-    for (int d = 0; d < 3; ++d)
-        for (int m = threadIdx.x; m < p.cnt[d]; m += kThreads) {
-            f0[d * fb + m] = F[d * fb + m];
-            f1[d * fb + m] = DF[d * fb + m];
-            gix[d * fb + m] = imod(p.lo[d] + m, ns[d]);
+    for (int e = threadIdx.x; e < nw[0] + nw[1] + nslot; e += kThreads) {
+        int d, t, slot;
+        if (e < nw[0]) {
+            d = 0, t = e, slot = e;
+        } else if (e < nw[0] + nw[1]) {
+            d = 1, t = e - nw[0], slot = t;
+        } else {
+            d = 2, slot = e - nw[0] - nw[1], t = slot - lead;
         }
+        const int nd = d == 0 ? n1 : (d == 1 ? n2 : n3);
+        const int cd = d == 0 ? p.cnt[0] : (d == 1 ? p.cnt[1] : p.cnt[2]);
+        const int wd_ = d == 0 ? nw[0] : (d == 1 ? nw[1] : nw[2]);
+        T s = T(0), sd = T(0);
+        if (t >= 0 && t < wd_)
+            for (int m = t; m < cd; m += nd) {
+                s += F[d * fb + m];
+                sd += DF[d * fb + m];
+            }
+        wf[d * ld + slot] = s;
+        wd[d * ld + slot] = sd;
+    }
     __syncthreads();
-    const int ia0 = (int)((long long)p.cnt[0] * slab / slabs), ia1 = (int)((long long)p.cnt[0] * (slab + 1) / slabs);
-    const int cc = p.cnt[2];
-    const int P = p.cnt[1] * cc;  // points of one a slice
-    const long long slice = (long long)a.n2 * a.n3;
+    const int ia0 = (int)((long long)nw[0] * slab / slabs), ia1 = (int)((long long)nw[0] * (slab + 1) / slabs);
+    const long long slice = (long long)n2 * n3;
+    const int npairs = nw[1] * ng;
+    const T* wa = wf;
+    const T* dwa = wd;
     T s0 = T(0), c0 = T(0), sx = T(0), cx = T(0), sy = T(0), cy = T(0), sz = T(0), cz = T(0);
-    if (P <= kThreads * kPT) {
-        // (b, c) points of this thread with their weights, reused for every slice
-        int off[kPT];  // offset within a slice: b n3 + c < 2^24
-        T w[kPT], wy[kPT], wz[kPT];
+    if (npairs <= kThreads * KP) {
+        int off[KP];  // b n3 + c of the pair's first point (< 2^24); pairs past the end read point 0 with zero weight
+        T wb[KP], dwb[KP], wc[KP][VW], dwc[KP][VW];
 #pragma unroll
-        for (int u = 0; u < kPT; ++u) {
-            const int pt = threadIdx.x + kThreads * u;
-            const bool ok = pt < P;
-            const int j = ok ? pt / cc : 0, k = ok ? pt - j * cc : 0;
-            off[u] = gix[fb + j] * a.n3 + gix[2 * fb + k];
-            w[u] = ok ? f0[fb + j] * f0[2 * fb + k] : T(0);
-            wy[u] = ok ? f1[fb + j] * f0[2 * fb + k] : T(0);
-            wz[u] = ok ? f0[fb + j] * f1[2 * fb + k] : T(0);
+        for (int u = 0; u < KP; ++u) {
+            const int pr = threadIdx.x + kThreads * u;
+            const bool ok = pr < npairs;
+            const int j = ok ? pr / ng : 0, g = ok ? pr - j * ng : 0;
+            int bj = st[1] + j;
+            if (bj >= n2) bj -= n2;
+            int cg = cst + g * VW;
+            if (cg >= n3) cg -= n3;
+            off[u] = ok ? bj * n3 + cg : 0;
+            wb[u] = ok ? wf[ld + j] : T(0);
+            dwb[u] = ok ? wd[ld + j] : T(0);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                wc[u][e] = wf[2 * ld + g * VW + e];
+                dwc[u][e] = wd[2 * ld + g * VW + e];
+            }
         }
-        for (int i = ia0; i < ia1; ++i) {
-            const T* Vs = V + gix[i] * slice;
-            T v[kPT];
+        // ring of kDepth slices of this thread's pairs in shared memory, filled by
+        // cp.async: each thread reads back only what it copied itself, so no barrier
+        T* ring = wf + ring_offset<T>(ld);
+        auto issue = [&](int t, int slot) {
+            int ai = st[0] + t;
+            if (ai >= n1) ai -= n1;
+            const T* Vs = V + ai * slice;
 #pragma unroll
-            for (int u = 0; u < kPT; ++u) v[u] = (threadIdx.x + kThreads * u < P) ? __ldg(Vs + off[u]) : T(0);
+            for (int u = 0; u < KP; ++u) {
+                const bool ok = threadIdx.x + kThreads * u < npairs;
+                cp_async<VW * sizeof(T)>(ring + ((slot * KP + u) * kThreads + threadIdx.x) * VW, Vs + off[u],
+                                         ok ? (int)(VW * sizeof(T)) : 0);
+            }
+        };
+#pragma unroll
+        for (int k = 0; k < kDepth - 1; ++k) {
+            if (ia0 + k < ia1) issue(ia0 + k, k);
+            cp_async_commit();
+        }
+        for (int t = ia0; t < ia1; ++t) {
+            const int k = t - ia0;
+            if (t + kDepth - 1 < ia1) issue(t + kDepth - 1, (k + kDepth - 1) % kDepth);
+            cp_async_commit();
+            cp_async_wait<kDepth - 1>();  // the group of slice t is complete
+            const T* r = ring + (k % kDepth) * KP * kThreads * VW;
             T p0 = T(0), py = T(0), pz = T(0);
 #pragma unroll
-            for (int u = 0; u < kPT; ++u) {
-                p0 += v[u] * w[u];
-                py += v[u] * wy[u];
-                pz += v[u] * wz[u];
+            for (int u = 0; u < KP; ++u) {
+                T v[VW];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) v[e] = r[(u * kThreads + threadIdx.x) * VW + e];
+                T r0 = T(0), r1 = T(0);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    r0 += v[e] * wc[u][e];
+                    r1 += v[e] * dwc[u][e];
+                }
+                p0 += wb[u] * r0;
+                py += dwb[u] * r0;
+                pz += wb[u] * r1;
             }
-            kahan_add(s0, c0, f0[i] * p0);
-            kahan_add(sx, cx, f1[i] * p0);
-            kahan_add(sy, cy, f0[i] * py);
-            kahan_add(sz, cz, f0[i] * pz);
+            kahan_add(s0, c0, wa[t] * p0);
+            kahan_add(sx, cx, dwa[t] * p0);
+            kahan_add(sy, cy, wa[t] * py);
+            kahan_add(sz, cz, wa[t] * pz);
         }
+        cp_async_wait<0>();
     } else {
-        // wide boxes: points revisited per slice with weights from shared memory
-        for (int i = ia0; i < ia1; ++i) {
-            const T* Vs = V + gix[i] * slice;
+        // very wide boxes: pairs revisited per slice with weights from shared memory
+        for (int t = ia0; t < ia1; ++t) {
+            int ai = st[0] + t;
+            if (ai >= n1) ai -= n1;
+            const T* Vs = V + ai * slice;
             T p0 = T(0), py = T(0), pz = T(0);
-            for (int pt = threadIdx.x; pt < P; pt += kThreads) {
-                const int j = pt / cc, k = pt - j * cc;
-                const T v = __ldg(Vs + (long long)gix[fb + j] * a.n3 + gix[2 * fb + k]);
-                p0 += v * f0[fb + j] * f0[2 * fb + k];
-                py += v * f1[fb + j] * f0[2 * fb + k];
-                pz += v * f0[fb + j] * f1[2 * fb + k];
+            for (int pr = threadIdx.x; pr < npairs; pr += kThreads) {
+                const int j = pr / ng, g = pr - j * ng;
+                int bj = st[1] + j;
+                if (bj >= n2) bj -= n2;
+                int cg = cst + g * VW;
+                if (cg >= n3) cg -= n3;
+                T v[VW];
+                VecLoad<T, VW>::ld(Vs + bj * n3 + cg, v);
+                T r0 = T(0), r1 = T(0);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    r0 += v[e] * wf[2 * ld + g * VW + e];
+                    r1 += v[e] * wd[2 * ld + g * VW + e];
+                }
+                p0 += wf[ld + j] * r0;
+                py += wd[ld + j] * r0;
+                pz += wf[ld + j] * r1;
             }
-            kahan_add(s0, c0, f0[i] * p0);
-            kahan_add(sx, cx, f1[i] * p0);
-            kahan_add(sy, cy, f0[i] * py);
-            kahan_add(sz, cz, f0[i] * pz);
+            kahan_add(s0, c0, wa[t] * p0);
+            kahan_add(sx, cx, dwa[t] * p0);
+            kahan_add(sy, cy, wa[t] * py);
+            kahan_add(sz, cz, wa[t] * pz);
         }
     }
     // four block sums: error-free FP32 warp steps, FP64 only across warps
@@ -180,6 +454,29 @@ cudaError_t prep_atoms(const Plan& p, const AtomArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t splat_prepared(const Plan& p, const AtomArgs<T>& a, void* rho, cudaStream_t s) {
+    if (p.use_bins) {
+        const int tA = p.tiles[0], tB = p.tiles[1], tC = p.tiles[2];
+        cudaError_t e = cudaSuccess;
+        if (a.n > 0) {
+            // leaf boxes too: a tile whose list is longer than the sort capacity selects from them
+            p.launches += 4;
+            k_leaf_boxes<T><<<(a.nleaves + 127) / 128, 128, 0, s>>>(a.prep, a.n, p.apl, a.nleaves, p.n[0], p.n[1],
+                                                                    p.n[2], p.leaf_box);
+            e = cudaMemsetAsync(p.bin_count, 0, sizeof(int) * p.n_tiles, s);
+            if (e != cudaSuccess) return e;
+            const unsigned nb = (unsigned)(((long long)a.n * 32 + 255) / 256);
+            k_bin<T, false><<<nb, 256, 0, s>>>(a, tA, tB, tC, p.bin_count, p.bin_off, p.bin_cursor, p.bin_list);
+            k_bin_scan<<<1, 1024, 0, s>>>(p.bin_count, p.n_tiles, p.bin_off, p.bin_cursor);
+            k_bin<T, true><<<nb, 256, 0, s>>>(a, tA, tB, tC, p.bin_count, p.bin_off, p.bin_cursor, p.bin_list);
+        } else {
+            e = cudaMemsetAsync(p.bin_count, 0, sizeof(int) * p.n_tiles, s);
+            if (e != cudaSuccess) return e;
+        }
+        p.launches += 1;
+        k_splat_binned<T><<<(unsigned)p.n_tiles, kThreads, 0, s>>>(a, static_cast<T*>(rho), tB, tC, p.bin_count,
+                                                                      p.bin_off, p.bin_list);
+        return cudaGetLastError();
+    }
     p.launches += (a.nleaves > 0 ? 1 : 0) + 1;
     if (a.nleaves > 0)
         k_leaf_boxes<T><<<(a.nleaves + 127) / 128, 128, 0, s>>>(a.prep, a.n, p.apl, a.nleaves, p.n[0], p.n[1],
@@ -200,7 +497,53 @@ cudaError_t splat_impl(const Plan& p, const double* pos, const double* q, int n,
     return splat_prepared<T>(p, a, rho, s);
 }
 
-size_t forces_smem(const Plan& p, size_t real_size) { return 3 * (size_t)p.box_max * (2 * real_size + sizeof(int)); }
+size_t forces_smem(const Plan& p, size_t real_size, int vw, int kp);
+int forces_kp(const Plan& p, int vw);
+
+// Pairs per thread: enough for the largest box of the plan (npairs <= box_max x
+// (box_max + 2 VW) / VW), at most 4; boxes beyond 4 x kThreads pairs loop over
+// them from shared memory.
+template <typename T, int VW>
+void launch_k_forces_vw(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs,
+                        cudaStream_t s) {
+    const int kp = forces_kp(p, VW);
+    const size_t sm = forces_smem(p, sizeof(T), VW, kp);
+    switch (kp) {
+        case 1: k_forces<T, VW, 1><<<blocks, kThreads, sm, s>>>(a, V, slabs, p.force_partials); break;
+        case 2: k_forces<T, VW, 2><<<blocks, kThreads, sm, s>>>(a, V, slabs, p.force_partials); break;
+        case 3: k_forces<T, VW, 3><<<blocks, kThreads, sm, s>>>(a, V, slabs, p.force_partials); break;
+        default: k_forces<T, VW, 4><<<blocks, kThreads, sm, s>>>(a, V, slabs, p.force_partials); break;
+    }
+}
+
+// The widest aligned vector along c: VW must divide N3 and V must be VW-element aligned.
+template <typename T>
+void launch_k_forces(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs, cudaStream_t s) {
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(V);
+    if constexpr (sizeof(T) == 4) {
+        if (p.n[2] % 4 == 0 && addr % 16 == 0) {
+            launch_k_forces_vw<T, 4>(p, a, V, blocks, slabs, s);
+            return;
+        }
+    }
+    if (addr % (2 * sizeof(T)) == 0)
+        launch_k_forces_vw<T, 2>(p, a, V, blocks, slabs, s);
+    else
+        launch_k_forces_vw<T, 1>(p, a, V, blocks, slabs, s);
+}
+
+size_t forces_smem(const Plan& p, size_t real_size, int vw, int kp) {
+    const int ld = p.box_max + 8;
+    const size_t ring = (size_t)kDepth * kp * kThreads * vw * real_size;
+    return (real_size == 4 ? ring_offset<float>(ld) : ring_offset<double>(ld)) * real_size + ring;
+}
+
+// Pairs per thread for the largest box of the plan, at most 4 (wider boxes loop over pairs).
+int forces_kp(const Plan& p, int vw) {
+    const long long rows = std::min(p.box_max, p.n[1]);
+    const long long npairs = rows * ((std::min(p.box_max, p.n[2]) + 3 * vw - 1) / vw);
+    return (int)std::min(4LL, (npairs + kThreads - 1) / kThreads);
+}
 
 template <typename T>
 cudaError_t forces_impl(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
@@ -215,15 +558,27 @@ cudaError_t forces_impl(const Plan& p, const double* pos, const double* q, int n
     int slabs = (4 * 152 * 2 + n - 1) / n;  // enough CTAs to cover the GPU
     if (slabs > p.max_force_slabs) slabs = p.max_force_slabs;
     if (slabs < 1) slabs = 1;
-    k_forces<T><<<(unsigned)n * slabs, kThreads, forces_smem(p, sizeof(T)), s>>>(a, static_cast<const T*>(vh), slabs,
-                                                                                 p.force_partials);
+    launch_k_forces<T>(p, a, static_cast<const T*>(vh), (unsigned)n * slabs, slabs, s);
     k_forces_finalize<<<(n + 127) / 128, 128, 0, s>>>(p.force_partials, n, slabs, q, p.dV, a.norm, a.inv_s2, f, phi);
     return cudaGetLastError();
 }
 
+template <typename T, int VW>
+cudaError_t allow_forces_smem(int optin) {
+    cudaError_t e = allow_max_dynamic_smem(k_forces<T, VW, 1>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 2>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 3>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 4>, optin);
+    return e;
+}
+
 template <typename T>
 cudaError_t configure_atoms(int optin) {
-    return allow_max_dynamic_smem(k_forces<T>, optin);
+    cudaError_t e = allow_forces_smem<T, 1>(optin);
+    if (e == cudaSuccess) e = allow_forces_smem<T, 2>(optin);
+    if constexpr (sizeof(T) == 4)
+        if (e == cudaSuccess) e = allow_forces_smem<T, 4>(optin);
+    return e;
 }
 
 }  // namespace
@@ -232,7 +587,9 @@ cudaError_t configure_atom_kernels(const Plan& p) {
     int optin = 0;
     cudaError_t e = optin_smem(&optin);
     if (e != cudaSuccess) return e;
-    if (forces_smem(p, p.real_size) + 1024 > (size_t)optin) return cudaErrorInvalidConfiguration;
+    for (int vw : {1, 2, 4})
+        if ((vw < 4 || p.real_size == 4) && forces_smem(p, p.real_size, vw, forces_kp(p, vw)) + 1024 > (size_t)optin)
+            return cudaErrorInvalidConfiguration;
     return p.prec == HARTREE_FP64 ? configure_atoms<double>(optin) : configure_atoms<float>(optin);
 }
 

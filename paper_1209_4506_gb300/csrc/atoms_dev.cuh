@@ -7,7 +7,6 @@
 
 namespace hartree {
 
-constexpr int TA = 16, TB = 8, TC = 32;  // splat tile (a, b, c)
 constexpr int kBatch = 32;               // atoms whose factors are staged at once
 constexpr int kPT = 12;                  // force gather: (b, c) points per thread held in registers
 
@@ -36,6 +35,7 @@ __device__ __forceinline__ void atom_prep_one(const AtomArgs<T>& a, int i) {
         const double lo = ceil((X - a.rc) / hs[d]);
         const double hi = floor((X + a.rc) / hs[d]);
         p.lo[d] = (int)lo;
+        p.st[d] = imod(p.lo[d], d == 0 ? a.n1 : (d == 1 ? a.n2 : a.n3));
         p.cnt[d] = hi >= lo ? min((int)(hi - lo) + 1, a.fb) : 0;
         const double D0 = lo * hs[d] - X;
         p.dh[d] = (T)D0;
@@ -114,12 +114,45 @@ __device__ __forceinline__ void leaf_box_one(const AtomPrep<T>* __restrict__ pre
     }
 }
 
-// Sum over the box points of one atom that land on grid index g (all images).
+// Sum over the box points of one atom that land on grid index g in [0, n) (all
+// images); st = lo mod n is the wrapped index of box point 0.
 template <typename T>
-__device__ __forceinline__ T image_sum(const T* __restrict__ f, int g, int lo, int cnt, int n) {
+__device__ __forceinline__ T image_sum(const T* __restrict__ f, int g, int st, int cnt, int n) {
+    int m = g - st;
+    if (m < 0) m += n;
     T s = T(0);
-    for (int m = imod(g - lo, n); m < cnt; m += n) s += f[m];
+    for (; m < cnt; m += n) s += f[m];
     return s;
+}
+
+// Stage the separable factors of atoms ids[0..nb) for the tile at (a0, b0, c0):
+// fa over TA a-points, fb over TB b-points, fc (times q (pi s^2)^-3/2) over TC
+// c-points.  One loop per axis, so the lanes of a warp take the same path.
+template <typename T>
+__device__ __forceinline__ void stage_factors(const AtomArgs<T>& a, const int* ids, int nb, int a0, int b0, int c0,
+                                              T (*fa)[TA], T (*fb)[TB], T (*fc)[TC]) {
+    for (int e = threadIdx.x; e < nb * TC; e += kThreads) {
+        const int t = e / TC, k = e - t * TC;
+        const int i = ids[t];
+        const AtomPrep<T>& p = a.prep[i];
+        const T sc = c0 + k < a.n3 ? image_sum(a.fac + ((long long)i * 3 + 2) * a.fb, c0 + k, p.st[2], p.cnt[2], a.n3)
+                                   : T(0);
+        fc[t][k] = p.qn * sc + p.ql * sc;
+    }
+    for (int e = threadIdx.x; e < nb * TA; e += kThreads) {
+        const int t = e / TA, f = e - t * TA;
+        const int i = ids[t];
+        const AtomPrep<T>& p = a.prep[i];
+        fa[t][f] = a0 + f < a.n1 ? image_sum(a.fac + (long long)i * 3 * a.fb, a0 + f, p.st[0], p.cnt[0], a.n1) : T(0);
+    }
+    for (int e = threadIdx.x; e < nb * TB; e += kThreads) {
+        const int t = e / TB, f = e - t * TB;
+        const int i = ids[t];
+        const AtomPrep<T>& p = a.prep[i];
+        fb[t][f] = b0 + f < a.n2
+                       ? image_sum(a.fac + ((long long)i * 3 + 1) * a.fb, b0 + f, p.st[1], p.cnt[1], a.n2)
+                       : T(0);
+    }
 }
 
 template <typename T>
@@ -188,21 +221,7 @@ __device__ void splat_tile(const AtomArgs<T>& a, T* __restrict__ rho, int tiles_
             const int nc = compact(atom >= 0, atom, cand);
             for (int bb = 0; bb < nc; bb += kBatch) {
                 const int nb = min(kBatch, nc - bb);
-                for (int e = threadIdx.x; e < nb * (TA + TB + TC); e += kThreads) {
-                    const int t = e / (TA + TB + TC), f = e - t * (TA + TB + TC);
-                    const int i = cand[bb + t];
-                    const AtomPrep<T>& p = a.prep[i];
-                    const T* F = a.fac + (long long)i * 3 * a.fb;
-                    if (f < TA) {
-                        fa[t][f] = image_sum(F, a0 + f, p.lo[0], p.cnt[0], a.n1);
-                    } else if (f < TA + TB) {
-                        fb[t][f - TA] = image_sum(F + a.fb, b0 + f - TA, p.lo[1], p.cnt[1], a.n2);
-                    } else {
-                        const int k = f - TA - TB;
-                        const T sc = image_sum(F + 2 * a.fb, c0 + k, p.lo[2], p.cnt[2], a.n3);
-                        fc[t][k] = p.qn * sc + p.ql * sc;
-                    }
-                }
+                stage_factors(a, cand + bb, nb, a0, b0, c0, fa, fb, fc);
                 __syncthreads();
                 for (int t = 0; t < nb; ++t) {
                     const T s = fb[t][warp] * fc[t][lane];

@@ -1,4 +1,5 @@
 // capi.cu -- plan creation and the extern "C" entry points of hartree.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -132,7 +133,7 @@ void free_plan(Plan& p) {
     void* ptrs[] = {p.W,           p.R,        p.tw[0],         p.tw[1], p.tw[2], p.twp[0], p.twp[1], p.twp[2], p.gsq[0],
                     p.gsq[1],      p.gsq[2],   p.eh_partials,   p.leaf_box,
                     p.atom_prep,   p.atom_fac, p.atom_dfac, p.force_partials, p.d_pos,   p.d_q,   p.d_f,   p.d_eh,
-                    p.d_err};
+                    p.d_err,       p.bin_count, p.bin_off, p.bin_cursor, p.bin_list};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -242,7 +243,22 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
     p.use_fast = fast_pass_mask(p);
     p.max_force_slabs = 1216;
 
+    // tile bins: an atom's box of at most box_max points meets at most box_max / T + 3 tiles along an axis
+    // (two wrapped segments, a partial last tile); the list is skipped when that bound is too large
+    {
+        const int T[3] = {TA, TB, TC};
+        long long per_atom = 1;
+        for (int i = 0; i < 3; ++i) {
+            p.tiles[i] = (p.n[i] + T[i] - 1) / T[i];
+            per_atom *= std::min(p.tiles[i], p.box_max / T[i] + 3);
+        }
+        p.n_tiles = p.tiles[0] * p.tiles[1] * p.tiles[2];
+        p.bin_cap = per_atom * p.max_atoms;
+        p.use_bins = p.bin_cap <= (1LL << 26);  // at most 256 MB of list
+        if (!p.use_bins) p.bin_cap = 0;
+    }
     const size_t ntot = (size_t)p.n[0] * p.n[1] * p.n[2];
+    const size_t nbin = p.use_bins ? (size_t)p.n_tiles : 0;
     struct Alloc {
         void** ptr;
         size_t bytes;
@@ -269,6 +285,10 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         {(void**)&p.d_f, (size_t)p.max_atoms * 3 * sizeof(double)},
         {(void**)&p.d_eh, sizeof(double)},
         {(void**)&p.d_err, sizeof(int)},
+        {(void**)&p.bin_count, (nbin + 1) * sizeof(int)},
+        {(void**)&p.bin_off, (nbin + 1) * sizeof(int)},
+        {(void**)&p.bin_cursor, (nbin + 1) * sizeof(int)},
+        {(void**)&p.bin_list, ((size_t)p.bin_cap + 1) * sizeof(int)},
     };
     for (auto& a : allocs) {
         cudaError_t e = cudaMalloc(a.ptr, a.bytes);

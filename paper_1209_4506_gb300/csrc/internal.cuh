@@ -13,6 +13,7 @@
 namespace hartree {
 
 constexpr int kThreads = 256;
+constexpr int TA = 16, TB = 8, TC = 32;  // splat tile (a, b, c)
 constexpr int kMaxAxis = 4096;       // largest grid size along one axis
 constexpr int kMaxBoxPoints = 1024;  // largest per-axis extent of one atom's cutoff box (points)
 
@@ -111,6 +112,7 @@ template <typename T>
 struct AtomPrep {
     int lo[3];   // first unwrapped grid index of the box along a, b, c
     int cnt[3];  // points of the box along a, b, c
+    int st[3];   // lo mod N: the wrapped grid index of the box's first point
     T dh[3];     // lo h - X, rounded to T
     T dl[3];     // (lo h - X) - dh (zero for FP64)
     T qn;        // q (pi s^2)^(-3/2), formed in FP64 and rounded once
@@ -181,6 +183,15 @@ struct Plan {
     bool tma_ok = false;      // tensor maps over W are valid
     CUtensorMap tmap_b, tmap_a;  // bit 0: c passes, bit 1: b passes, bit 2: a pass use the specialised kernels
     size_t smem_c, smem_b, smem_a;
+    // tile binning of the splat: per 16 x 8 x 32 tile the atoms whose cutoff box reaches it (CSR)
+    bool use_bins = false;     // false: the splat selects atoms per tile from the leaf boxes
+    int tiles[3] = {0, 0, 0};  // tiles along a, b, c
+    int n_tiles = 0;
+    long long bin_cap = 0;      // capacity of bin_list (a bound on the (atom, tile) pairs)
+    int* bin_count = nullptr;   // [n_tiles]
+    int* bin_off = nullptr;     // [n_tiles + 1]
+    int* bin_cursor = nullptr;  // [n_tiles]
+    int* bin_list = nullptr;    // [bin_cap]
 };
 
 // Let kernel `f` use all of the device's opt-in shared memory that its static

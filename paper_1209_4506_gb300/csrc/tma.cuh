@@ -85,6 +85,26 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// ---------------------------------------------------------------- per-thread async copies
+// global -> shared copy of `bytes` (4, 8 or 16) bytes, of which the first `src_bytes`
+// are read and the rest zero-filled (src_bytes = 0: a zero-filled slot, src unread)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int src_bytes) {
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+                     "r"(src_bytes)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed copy groups are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Host: encode a 3D FP32 tiled tensor map (dims innermost first, strides in bytes for dims 1, 2).
 bool encode_tensor_map_3d(CUtensorMap* map, void* base, const uint64_t dims[3], const uint64_t strides[2],
                           const uint32_t box[3]);

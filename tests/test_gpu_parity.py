@@ -320,3 +320,15 @@ def test_autotune_cache_roundtrip(tmp_path):
     assert first == again
     import json
     assert len(json.load(open(path))) == 1
+
+
+def test_dense_tile_beyond_the_bin_sort_capacity():
+    # 1100 atoms in a cell of one splat tile: the tile's list is longer than the
+    # binned splat sorts in shared memory, so that tile takes the leaf-selecting path
+    S = synth.random_system((16, 8, 32), (3.0, 2.0, 5.0), 1100, 0.6, seed=21, precision="fp32")
+    ref = O.solve_system(S)
+    g = gpu_step(S, "fp32")
+    assert rel_l2(g["rho"], ref["rho"]) <= 2e-6
+    assert rel_l2(g["vh"], ref["vh"]) <= TOL["fp32"]["v"]
+    assert abs(g["eh"] - ref["eh"]) <= TOL["fp32"]["e"] * abs(ref["eh"])
+    assert np.max(np.abs(g["forces"] - ref["forces"])) <= TOL["fp32"]["f"]
