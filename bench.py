@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default="diamond512", choices=["diamond512", "diamond256"],
                     help="diamond256: the 4x4x4 cell on 256^3 (same density and sigma), for small profiler captures")
     ap.add_argument("--skip-side", action="store_true", help="skip the e2e, adjoint and batched measurements")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16split"],
+                    help="bf16split: b passes on the tensor cores (N2 = 256: the diamond256 workload)")
     return ap.parse_args()
 
 
@@ -346,7 +348,7 @@ def main():
     perm, _ = atoms_reorder(S.pos, (S.n_atoms + apl - 1) // apl)
     reorder_ms = 1e3 * (time.perf_counter() - t0)
     pos_h, q_h = S.pos[perm], S.q[perm]
-    plan = HartreePlan(S.n, S.cell, S.sigma, "fp32", atoms_per_leaf=apl, max_atoms=S.n_atoms)
+    plan = HartreePlan(S.n, S.cell, S.sigma, args.precision, atoms_per_leaf=apl, max_atoms=S.n_atoms)
     variants = plan.autotune()
     pos = torch.tensor(pos_h, device=dev)
     q = torch.tensor(q_h, device=dev)
@@ -448,7 +450,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl_text + ", FP32: splat + Poisson + E_H + forces",
+            "config": {"workload": wl_text + (", FP32" if args.precision == "fp32" else
+                                              ", FP32 with tensor-core split b passes") +
+                                   ": splat + Poisson + E_H + forces",
                        "grid": list(S.n), "atoms": S.n_atoms, "yardstick_bytes_per_step": ybytes,
                        "l2": "inputs larger than L2 (each grid array 0.5 GB)" if S.n[0] == 512 else
                              "working set larger than L2 (three 64 MB grid arrays); profiling case",

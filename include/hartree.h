@@ -50,7 +50,8 @@ typedef struct hartree_batch_s* hartree_batch;
 typedef enum {
     HARTREE_FP64 = 0,          /* FP64 transforms and grids                          */
     HARTREE_FP32 = 1,          /* FP32 transforms and grids, FP64 E_H and forces      */
-    HARTREE_FP32_TC_SPLIT = 2  /* FP32, radix-16 stages on BF16 tensor cores (hi/lo) */
+    HARTREE_FP32_TC_SPLIT = 2  /* FP32; the b passes run as two radix-16 stages on the BF16
+                                  tensor cores with hi/lo split operands (N2 must be 256)   */
 } hartree_precision;
 
 typedef enum {
@@ -72,8 +73,13 @@ typedef struct {
     int precision;        /* a hartree_precision                                            */
     int atoms_per_leaf;   /* atoms per bisection leaf used by the splat; 0 = default 16     */
     int max_atoms;        /* largest atom count any call on this plan will pass; 0 = 65536 */
-    unsigned flags;       /* reserved, must be 0                                            */
+    unsigned flags;       /* 0, or HARTREE_FLAG_TC_BF16 with HARTREE_FP32_TC_SPLIT           */
 } hartree_desc;
+
+/* HARTREE_FP32_TC_SPLIT operands: FP16 hi/lo pairs with a power-of-two scale per
+ * row by default (about 2^-22 relative per product); this flag selects BF16
+ * hi/lo pairs instead (about 2^-16 relative per product, no scaling). */
+#define HARTREE_FLAG_TC_BF16 1u
 
 /* ---------------------------------------------------------------- plans */
 

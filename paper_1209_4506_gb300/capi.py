@@ -26,6 +26,8 @@ HARTREE_ERR_OOM = 4
 HARTREE_ERR_TIMEOUT = 5
 HARTREE_ERR_NOT_CAPTURABLE = 6
 
+HARTREE_FLAG_TC_BF16 = 1
+
 # Every symbol the public header declares (the CPU tests check the exports).
 EXPORTED = (
     "hartree_plan_create",

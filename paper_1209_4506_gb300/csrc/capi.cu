@@ -133,7 +133,7 @@ void free_plan(Plan& p) {
     void* ptrs[] = {p.W,           p.R,        p.tw[0],         p.tw[1], p.tw[2], p.twp[0], p.twp[1], p.twp[2], p.gsq[0],
                     p.gsq[1],      p.gsq[2],   p.eh_partials,   p.leaf_box,
                     p.atom_prep,   p.atom_fac, p.atom_dfac, p.force_partials, p.d_pos,   p.d_q,   p.d_f,   p.d_eh,
-                    p.d_err,       p.bin_count, p.bin_off, p.bin_cursor, p.bin_list};
+                    p.d_err,       p.bin_count, p.bin_off, p.bin_cursor, p.bin_list, p.tc_dft};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -165,11 +165,11 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
     if (!desc || !out) return fail(HARTREE_ERR_INVALID, "plan_create: null argument");
     *out = nullptr;
     const hartree_desc& d = *desc;
-    if (d.flags != 0) return fail(HARTREE_ERR_INVALID, "plan_create: flags must be 0");
+    if (d.flags & ~HARTREE_FLAG_TC_BF16) return fail(HARTREE_ERR_INVALID, "plan_create: unknown flags");
+    if ((d.flags & HARTREE_FLAG_TC_BF16) && d.precision != HARTREE_FP32_TC_SPLIT)
+        return fail(HARTREE_ERR_INVALID, "plan_create: HARTREE_FLAG_TC_BF16 needs HARTREE_FP32_TC_SPLIT");
     if (d.precision != HARTREE_FP64 && d.precision != HARTREE_FP32 && d.precision != HARTREE_FP32_TC_SPLIT)
         return fail(HARTREE_ERR_INVALID, "plan_create: unknown precision %d", d.precision);
-    if (d.precision == HARTREE_FP32_TC_SPLIT)
-        return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: HARTREE_FP32_TC_SPLIT is not available in this build");
     for (int i = 0; i < 3; ++i) {
         if (d.n[i] < 2 || d.n[i] > kMaxAxis || !smooth235(d.n[i]))
             return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: N%d = %d is not a 2/3/5-smooth size in [2, %d]",
@@ -194,6 +194,10 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         p.n[i] = d.n[i];
         p.L[i] = d.cell[i];
         p.h[i] = d.cell[i] / d.n[i];
+    }
+    if (p.prec == HARTREE_FP32_TC_SPLIT && !tc_split_supported(p)) {
+        delete h;
+        return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: HARTREE_FP32_TC_SPLIT needs N2 = 256 (got %d)", p.n[1]);
     }
     p.M = p.n[2] / 2;
     p.nh = p.M + 1;
@@ -289,6 +293,7 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         {(void**)&p.bin_off, (nbin + 1) * sizeof(int)},
         {(void**)&p.bin_cursor, (nbin + 1) * sizeof(int)},
         {(void**)&p.bin_list, ((size_t)p.bin_cap + 1) * sizeof(int)},
+        {&p.tc_dft, p.prec == HARTREE_FP32_TC_SPLIT ? tc_table_bytes() : 16},
     };
     for (auto& a : allocs) {
         cudaError_t e = cudaMalloc(a.ptr, a.bytes);
@@ -314,6 +319,8 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         cudaError_t e = configure_poisson_kernels(p);
         if (e == cudaSuccess) e = configure_fast_kernels(p);
         if (e == cudaSuccess) e = configure_atom_kernels(p);
+        if (e == cudaSuccess) e = configure_tc_kernels(p);
+        if (e == cudaSuccess) e = upload_tc_tables(p);
         if (e != cudaSuccess) st = cuda_fail(e, "plan_create: kernel attributes");
     }
     if (st != HARTREE_OK) {
@@ -437,6 +444,7 @@ int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice) {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     static const int passes[3][2] = {{0, 4}, {1, 3}, {2, 2}};
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        if (k == 1 && p.prec == HARTREE_FP32_TC_SPLIT) continue;  // b passes run on the tensor cores
         const int nv = fast_variants(p, k);
         if (nv <= 1) continue;
         float best = 1e30f;

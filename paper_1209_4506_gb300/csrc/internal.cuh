@@ -192,6 +192,7 @@ struct Plan {
     int* bin_off = nullptr;     // [n_tiles + 1]
     int* bin_cursor = nullptr;  // [n_tiles]
     int* bin_list = nullptr;    // [bin_cap]
+    void* tc_dft = nullptr;     // HARTREE_FP32_TC_SPLIT: BF16 hi/lo 16-point DFT operands (forward, inverse)
 };
 
 // Let kernel `f` use all of the device's opt-in shared memory that its static
@@ -229,6 +230,12 @@ int fast_variants(const Plan& p, int kind);  // kind 0: c passes, 1: b passes, 2
 void prepare_tma(Plan& p);                   // encode the tensor maps of the TMA-streamed passes
 long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
 cudaError_t configure_atom_kernels(const Plan& p);
+// tensor-core b passes of HARTREE_FP32_TC_SPLIT plans (tc_split.cu)
+bool tc_split_supported(const Plan& p);
+size_t tc_table_bytes();
+cudaError_t upload_tc_tables(const Plan& p);
+cudaError_t configure_tc_kernels(const Plan& p);
+long long launch_tc_pass(const Plan& p, int pass, cudaStream_t s);
 
 }  // namespace hartree
 

@@ -62,6 +62,7 @@ template <typename T>
 long long pass_impl(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s) {
     const int bit = (pass == 0 || pass == 4) ? 1 : ((pass == 1 || pass == 3) ? 2 : 4);
     ++p.launches;
+    if (p.prec == HARTREE_FP32_TC_SPLIT && (pass == 1 || pass == 3)) return launch_tc_pass(p, pass, s);
     if (p.use_fast & bit) return launch_fast_pass(p, pass, rho, vh, s);
     PoissonArgs<T> a = make_args<T>(p);
     const long long nlines = (long long)p.n[0] * p.n[1];

@@ -54,6 +54,7 @@ class HartreePlan:
         atoms_per_leaf: int = 0,
         max_atoms: int = 0,
         device=None,
+        flags: int = 0,
     ):
         torch = _torch()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
@@ -71,7 +72,7 @@ class HartreePlan:
         d.precision = _PREC[precision]
         d.atoms_per_leaf = int(atoms_per_leaf)
         d.max_atoms = int(max_atoms)
-        d.flags = 0
+        d.flags = int(flags)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             capi.check(capi.hartree_plan_create(ctypes.byref(d), ctypes.byref(h)))

@@ -190,3 +190,10 @@ def test_batch_create_rejects_before_any_device_work():
     assert capi.hartree_batch_offsets(None, None, None) == capi.HARTREE_ERR_INVALID
     assert capi.hartree_batch_device_status(None) == capi.HARTREE_ERR_INVALID
     capi.hartree_batch_destroy(None)
+
+
+def test_split_precision_requires_n2_256():
+    d = _fp32_desc(capi.HARTREE_FP32_TC_SPLIT)  # 48^3
+    h = ctypes.c_void_p()
+    assert capi.hartree_plan_create(ctypes.byref(d), ctypes.byref(h)) == capi.HARTREE_ERR_UNSUPPORTED_SIZE
+    assert b"N2 = 256" in capi.hartree_last_error()
