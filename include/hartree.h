@@ -211,13 +211,15 @@ int hartree_plan_device_status(hartree_plan plan);
  * Kernel variants: each pass kind (0: the two c passes, 1: the two b passes,
  * 2: the a pass) may have several compiled tile shapes (columns or lines per
  * CTA and threads per CTA); for FP32 b and a passes of 256 or 512 points
- * variant 2 is the persistent kernel that streams tiles with TMA bulk copies.  hartree_plan_autotune times every variant on the
- * plan's own workspace (overwriting it; waits for the stream; not capturable)
- * and keeps the fastest; choice[3] (host, may be NULL) receives the picks.
- * hartree_plan_set_variants applies picks saved earlier (e.g. from a cache);
- * out-of-range picks return HARTREE_ERR_INVALID.  Every variant applies the
- * same operations to each element, so V_H is identical across variants; E_H
- * sums its terms in a different grouping and agrees to rounding.
+ * variants 2 and up are persistent kernels that stream tiles with TMA bulk
+ * copies, those past the first with radix-32 stages.  hartree_plan_autotune
+ * times every variant on the plan's own workspace (overwriting it; waits for
+ * the stream; not capturable) and keeps the fastest; choice[3] (host, may be
+ * NULL) receives the picks.  hartree_plan_set_variants applies picks saved
+ * earlier (e.g. from a cache); out-of-range picks return HARTREE_ERR_INVALID.
+ * Variants 0..2 apply the same operations to each element, so V_H is
+ * identical across them; the radix-32 variants round differently; every
+ * variant stays within the precision's tolerance.
  */
 int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice);
 int hartree_plan_set_variants(hartree_plan plan, const int* choice);

@@ -451,11 +451,20 @@ struct ColTmaCfg {
     }
 };
 
+// TMA variants by line length: thread counts and radix orders (radix 32 stages
+// halve the twiddle multiplies and shared-memory round trips of 8 x 8 x 8).
 template <class F>
-bool with_col_tma_cfg(int n, F&& f) {
+bool with_col_tma_cfg(int n, int variant, F&& f) {
     switch (n) {
-        case 256: f(ColTmaCfg<256, 16, 16, 1, 3>{}); return true;
-        case 512: f(ColTmaCfg<512, 8, 8, 8, 3>{}); return true;
+        case 256:
+            if (variant == 1) f(ColTmaCfg<128, 32, 8, 1, 3>{});
+            else f(ColTmaCfg<256, 16, 16, 1, 3>{});
+            return true;
+        case 512:
+            if (variant == 1) f(ColTmaCfg<256, 32, 16, 1, 3>{});
+            else if (variant == 2) f(ColTmaCfg<256, 16, 32, 1, 3>{});
+            else f(ColTmaCfg<512, 8, 8, 8, 3>{});
+            return true;
         default: return false;
     }
 }
@@ -485,10 +494,11 @@ bool with_col_cfg(int n, int variant, F&& f) {
     }
 }
 int col_variants(int n) { return (n == 256 || n == 512) ? 2 : 1; }
+int col_tma_variants(int n) { return n == 512 ? 3 : (n == 256 ? 2 : 0); }
 
-// Variant 2 of the b / a passes: the TMA-streamed kernel (FP32, plan has the tensor maps).
+// Variants col_variants(n) .. of the b / a passes: the TMA-streamed kernels (FP32, plan has the tensor maps).
 bool col_tma_available(const Plan& p, int axis) {
-    return p.prec != HARTREE_FP64 && p.tma_ok && with_col_tma_cfg(p.n[axis], [](auto) {});
+    return p.prec != HARTREE_FP64 && p.tma_ok && with_col_tma_cfg(p.n[axis], 0, [](auto) {});
 }
 
 // c-pass configurations by M = N3 / 2 and variant (variant 1: half the lines per CTA).
@@ -569,8 +579,9 @@ cudaError_t configure_fast_t(const Plan& p, int optin) {
     for (int v = 0; v < col_variants(p.n[1]); ++v) with_col_cfg<T>(p.n[1], v, cfg);
     for (int v = 0; v < col_variants(p.n[0]); ++v) with_col_cfg<T>(p.n[0], v, cfg);
     if constexpr (sizeof(T) == 4) {
-        if (col_tma_available(p, 1)) with_col_tma_cfg(p.n[1], cfg);
-        if (col_tma_available(p, 0)) with_col_tma_cfg(p.n[0], cfg);
+        for (int ax = 0; ax < 2; ++ax)
+            if (col_tma_available(p, ax))
+                for (int v = 0; v < col_tma_variants(p.n[ax]); ++v) with_col_tma_cfg(p.n[ax], v, cfg);
     }
     return e;
 }
@@ -598,9 +609,10 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
     const int axis = (pass == 2) ? 0 : 1;  // transformed axis: a for pass 2, b for passes 1 and 3
     const int kind = (pass == 2) ? 2 : 1;
     if constexpr (sizeof(T) == 4) {
-        if (p.var[kind] == 2 && col_tma_available(p, axis)) {
-            // variant 2: TMA-streamed persistent kernel, one CTA per SM
-            with_col_tma_cfg(p.n[axis], [&](auto c) {
+        const int tv = p.var[kind] - col_variants(p.n[axis]);
+        if (tv >= 0 && col_tma_available(p, axis)) {
+            // TMA-streamed persistent kernel, one CTA per SM
+            with_col_tma_cfg(p.n[axis], tv, [&](auto c) {
                 const int chunks = (p.nh + c.cols - 1) / c.cols;
                 const int ntiles = p.n[1 - axis] * chunks;
                 grid = ntiles < p.sm_count ? ntiles : p.sm_count;
@@ -624,8 +636,9 @@ long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, c
 
 int fast_variants(const Plan& p, int kind) {
     if (kind == 0) return (p.use_fast & 1) ? line_variants(p.M) : 1;
-    if (kind == 1) return (p.use_fast & 2) ? (col_tma_available(p, 1) ? 3 : col_variants(p.n[1])) : 1;
-    return (p.use_fast & 4) ? (col_tma_available(p, 0) ? 3 : col_variants(p.n[0])) : 1;
+    const int ax = kind == 1 ? 1 : 0;
+    if (!(p.use_fast & (kind == 1 ? 2 : 4))) return 1;
+    return col_variants(p.n[ax]) + (col_tma_available(p, ax) ? col_tma_variants(p.n[ax]) : 0);
 }
 
 // ------------------------------------------------------------------ host: tensor maps

@@ -275,7 +275,11 @@ def test_single_passes_reproduce_solve_density(precision):
     "shape,precision", [((512, 256, 512), "fp32"), ((256, 512, 256), "fp32"), ((256, 512, 256), "fp64")]
 )
 def test_kernel_variants_give_identical_potential(shape, precision):
-    """Every compiled tile shape (and the TMA-streamed passes) computes the same V_H."""
+    """Every compiled tile shape and radix order (and the TMA-streamed passes) computes V_H within tolerance.
+
+    Variants 0..2 keep the radix order of the plain kernels (tile shapes and the
+    TMA stream differ only in which thread does a butterfly), so their V_H is
+    bit-identical; the radix-32 TMA variants (3, 4) round differently."""
     import itertools
 
     from paper_1209_4506_gb300 import capi
@@ -287,7 +291,7 @@ def test_kernel_variants_give_identical_potential(shape, precision):
     v_ref, e_ref, _, _ = O.poisson(cell, rho.double().cpu().numpy())
     plan = HartreePlan(shape, cell, 0.5, precision)
     results = []
-    for choice in itertools.product(range(3), repeat=3):
+    for choice in itertools.product(range(5), repeat=3):
         try:
             plan.set_variants(list(choice))
         except capi.HartreeError:
@@ -299,13 +303,14 @@ def test_kernel_variants_give_identical_potential(shape, precision):
     assert len(results) >= 8
     for choice, vh, eh in results:
         assert rel_l2(vh.double().cpu().numpy(), v_ref) <= TOL[precision]["v"], choice
-        assert torch.equal(vh, results[0][1]), choice
-        # E_H: same terms, different grouping (per-CTA partials, persistent CTAs sum across tiles)
-        assert abs(eh - results[0][2]) <= 1e-10 * abs(results[0][2]), choice
-    assert abs(results[0][2] - e_ref) <= WHITE_NOISE_E_TOL[precision] * abs(e_ref)
+        assert abs(eh - e_ref) <= WHITE_NOISE_E_TOL[precision] * abs(e_ref), choice
+        if max(choice) <= 2:
+            assert torch.equal(vh, results[0][1]), choice
+            # E_H: same terms, different grouping (per-CTA partials, persistent CTAs sum across tiles)
+            assert abs(eh - results[0][2]) <= 1e-10 * abs(results[0][2]), choice
     picks = plan.autotune()
     plan.device_status()
-    assert all(0 <= p <= 2 for p in picks)
+    assert all(0 <= p <= 4 for p in picks)
     with pytest.raises(capi.HartreeError):
         plan.set_variants([0, 0, 5])
 
