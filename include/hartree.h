@@ -25,6 +25,13 @@
  *               HARTREE_FP64 -> double, HARTREE_FP32 -> float,
  *               HARTREE_FP32_TC_SPLIT -> float.  Positions, charges, energies
  *               and forces are always double.
+ *   Alignment   the Poisson passes move grid lines as (re, im) pairs of the
+ *               element type, so every grid buffer read or written by a solve
+ *               (rho, vh) must start on a multiple of twice the element size:
+ *               8 bytes for float, 16 for double.  Calls given a grid that is
+ *               not return HARTREE_ERR_INVALID before any device work.  Grids
+ *               that are also 16-byte aligned (any cudaMalloc or torch tensor
+ *               start) let FP32 plans stream the c passes with bulk copies.
  *   Memory      "device" pointers are CUDA global memory of the current device,
  *               owned by the caller.  The plan owns its workspace, allocated
  *               once in hartree_plan_create; the per-solve calls allocate

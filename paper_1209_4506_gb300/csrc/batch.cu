@@ -285,6 +285,8 @@ extern "C" int hartree_batch_offsets(hartree_batch batch, long long* grid_off, i
 extern "C" int hartree_solve_batched(hartree_batch batch, const double* pos, const double* q, void* vh, double* eh,
                                      void* stream) {
     if (!batch || !vh || !eh) return batch_fail(HARTREE_ERR_INVALID, "solve_batched: null argument");
+    if (reinterpret_cast<uintptr_t>(vh) % 8 != 0)  // grid lines move as (re, im) float pairs
+        return batch_fail(HARTREE_ERR_INVALID, "solve_batched: vh must be aligned to 8 bytes");
     BatchHost& h = batch->h;
     if (h.atom_off[h.n_cells] > 0 && (!pos || !q))
         return batch_fail(HARTREE_ERR_INVALID, "solve_batched: null atom arrays");

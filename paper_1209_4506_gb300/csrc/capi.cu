@@ -341,6 +341,12 @@ void hartree_plan_destroy(hartree_plan plan) {
 
 unsigned long long hartree_plan_workspace_bytes(hartree_plan plan) { return plan ? plan->p.bytes : 0ULL; }
 
+// The c passes move grid lines as (re, im) pairs of the plan's real type: a grid that a
+// solve reads or writes must start on a multiple of twice the element size.
+static bool grid_aligned(const Plan& p, const void* g) {
+    return g == nullptr || reinterpret_cast<uintptr_t>(g) % (2 * p.real_size) == 0;
+}
+
 int hartree_splat(hartree_plan plan, const double* pos, const double* q, int n, void* rho, void* stream) {
     if (!plan || !rho || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "splat: null argument");
     if (n < 0 || n > plan->p.max_atoms)
@@ -351,6 +357,8 @@ int hartree_splat(hartree_plan plan, const double* pos, const double* q, int n, 
 
 int hartree_solve_density(hartree_plan plan, const void* rho, void* vh, double* eh, void* stream) {
     if (!plan || !rho || !vh) return fail(HARTREE_ERR_INVALID, "solve_density: null argument");
+    if (!grid_aligned(plan->p, rho) || !grid_aligned(plan->p, vh))
+        return fail(HARTREE_ERR_INVALID, "solve_density: grids must be aligned to %d bytes", (int)(2 * plan->p.real_size));
     cudaError_t e = launch_poisson(plan->p, rho, vh, eh, (cudaStream_t)stream);
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "solve_density");
 }
@@ -360,6 +368,8 @@ int hartree_solve(hartree_plan plan, const double* pos, const double* q, int n, 
     if (!plan || !vh || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "solve: null argument");
     if (n < 0 || n > plan->p.max_atoms)
         return fail(HARTREE_ERR_INVALID, "solve: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
+    if (!grid_aligned(plan->p, rho) || !grid_aligned(plan->p, vh))
+        return fail(HARTREE_ERR_INVALID, "solve: grids must be aligned to %d bytes", (int)(2 * plan->p.real_size));
     void* dens = rho ? rho : vh;
     cudaError_t e = launch_splat(plan->p, pos, q, n, dens, (cudaStream_t)stream);
     if (e == cudaSuccess) e = launch_poisson(plan->p, dens, vh, eh, (cudaStream_t)stream);
@@ -387,6 +397,8 @@ int hartree_step(hartree_plan plan, const double* pos, const double* q, int n, v
     if (!plan || !vh || (n > 0 && (!pos || !q || !f))) return fail(HARTREE_ERR_INVALID, "step: null argument");
     if (n < 0 || n > plan->p.max_atoms)
         return fail(HARTREE_ERR_INVALID, "step: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
+    if (!grid_aligned(plan->p, rho) || !grid_aligned(plan->p, vh))
+        return fail(HARTREE_ERR_INVALID, "step: grids must be aligned to %d bytes", (int)(2 * plan->p.real_size));
     cudaStream_t s = (cudaStream_t)stream;
     void* dens = rho ? rho : vh;
     cudaError_t e = launch_splat(plan->p, pos, q, n, dens, s);
@@ -399,6 +411,8 @@ int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, v
     if (!plan) return fail(HARTREE_ERR_INVALID, "solve_pass: null plan");
     if (pass < 0 || pass > 4) return fail(HARTREE_ERR_INVALID, "solve_pass: pass %d not in 0..4", pass);
     if ((pass == 0 && !rho) || (pass == 4 && !vh)) return fail(HARTREE_ERR_INVALID, "solve_pass: null grid");
+    if ((pass == 0 && !grid_aligned(plan->p, rho)) || (pass == 4 && !grid_aligned(plan->p, vh)))
+        return fail(HARTREE_ERR_INVALID, "solve_pass: grids must be aligned to %d bytes", (int)(2 * plan->p.real_size));
     cudaError_t e = launch_poisson_pass(plan->p, pass, rho, vh, (cudaStream_t)stream);
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "solve_pass");
 }

@@ -13,6 +13,9 @@
 //     butterflies use them and split constants, so FP32 rounding carries no
 //     systematic magnitude bias into E_H; the inverse transforms only shape
 //     V_H and use the plain values.
+#include <algorithm>
+#include <type_traits>
+
 #include "internal.cuh"
 #include "tma.cuh"
 
@@ -87,10 +90,10 @@ struct LineRealOut {
 };
 
 // Z[k] = (X[k] + conj X[M-k]) + i w^-k (X[k] - conj X[M-k]) from the half spectrum (c2r pre-step)
-template <typename T>
+template <typename T, class Tw = const TwPair<T>*>
 struct LineC2RIn {
     const cpx<T>* x;
-    const TwPair<T>* tw;  // exp(-2 pi i k / N3)
+    Tw tw;  // exp(-2 pi i k / N3)
     int M;
     bool act;
     __device__ __forceinline__ cpx<T> ld_(int, int k) const {
@@ -108,12 +111,24 @@ struct NoPost {
     __device__ __forceinline__ void operator()(int, int, cpx<T>&) const {}
 };
 
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// Twiddles held as rounded values only (the inverse transforms use no low parts).
+template <typename T>
+struct TwHi {
+    const cpx<T>* p;
+    __device__ __forceinline__ TwPair<T> operator[](int i) const { return TwPair<T>{p[i], mk(T(0), T(0))}; }
+};
+
 // One Stockham stage (radix R, sub-transform NS) for the BPT butterflies
-// j = j0 + t JSTEP of this thread; SYNC when src and dst share storage.
+// j = j0 + t JSTEP of this thread; SYNC when src and dst share storage (or when
+// `hook` must run once every thread has read src: it runs after that barrier).
 template <typename T, int N, int R, int NS, int BPT, int JSTEP, int TWS, bool INV, bool SYNC, class Src, class Dst,
-          class Post>
-__device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, int j0, const TwPair<T>* TW,
-                                       const Post& post) {
+          class Post, class Tw, class Hook = NoHook>
+__device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, int j0, const Tw& TW,
+                                       const Post& post, const Hook& hook = Hook{}) {
     constexpr int NB = N / R;
     cpx<T> v[BPT][R];
 #pragma unroll
@@ -122,7 +137,13 @@ __device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, 
 #pragma unroll
         for (int r = 0; r < R; ++r) v[t][r] = src.ld_(col, j + r * NB);
     }
-    if constexpr (SYNC) __syncthreads();
+    if constexpr (SYNC) {
+        // a hook may hand src to the async proxy (a bulk copy refilling it): order this
+        // thread's reads of src before that write
+        if constexpr (!std::is_same<Hook, NoHook>::value) fence_proxy_async_smem();
+        __syncthreads();
+        hook();
+    }
 #pragma unroll
     for (int t = 0; t < BPT; ++t) {
         const int j = j0 + t * JSTEP;
@@ -144,23 +165,83 @@ __device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, 
 // Whole transform of a tile: stage 0 from src, the rest in place in `sm`,
 // the last stage through `post` into dst.  Threads: col, j0 in [0, JSTEP).
 template <typename T, int R0, int R1, int R2, int JSTEP, int TWS, bool INV, bool FIRST_SYNC, class Src, class Sm,
-          class Dst, class Post>
+          class Dst, class Post, class Tw, class Hook = NoHook>
 __device__ __forceinline__ void ftransform(const Src& src, const Sm& sm, const Dst& dst, int col, int j0,
-                                           const TwPair<T>* TW, const Post& post) {
+                                           const Tw& TW, const Post& post, const Hook& hook = Hook{}) {
     constexpr int N = R0 * R1 * R2;
     constexpr int B0 = (N / R0) / JSTEP, B1 = (N / R1) / JSTEP, B2 = (N / R2) / JSTEP;
     static_assert(B0 * JSTEP * R0 == N && B1 * JSTEP * R1 == N, "butterflies must divide evenly");
     if constexpr (R2 == 1) {
-        fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{});
+        fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{}, hook);
         __syncthreads();
         fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, dst, col, j0, TW, post);
     } else {
         static_assert(B2 * JSTEP * R2 == N, "butterflies must divide evenly");
-        fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{});
+        fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{}, hook);
         __syncthreads();
         fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, sm, col, j0, TW, NoPost{});
         __syncthreads();
         fstage<T, N, R2, R0 * R1, B2, JSTEP, TWS, INV, true>(sm, dst, col, j0, TW, post);
+    }
+}
+
+// The last forward stage (radix R, so j < N / R, k = j and the outputs sit at
+// j + r N / R), the Green multiply `green` on each output, and the first
+// stage of the inverse transform.  The inverse takes the radices in the
+// reverse order, so its first stage (radix R, no twiddles) reads exactly the
+// points the forward stage leaves in this thread's registers: the two stages
+// and the multiply run back to back with no shared-memory round trip.
+template <typename T, int N, int R, int BPT, int JSTEP, class Sm, class Tw, class Green>
+__device__ __forceinline__ void fstage_green_pivot(const Sm& sm, int col, int j0, const Tw& TW, const Green& green) {
+    constexpr int NS = N / R;
+    cpx<T> v[BPT][R];
+#pragma unroll
+    for (int t = 0; t < BPT; ++t) {
+        const int j = j0 + t * JSTEP;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[t][r] = sm.ld_(col, j + r * NS);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < BPT; ++t) {
+        const int j = j0 + t * JSTEP;
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[t][r] = twmul<true>(v[t][r], TW[j * r], false);
+        }
+        dft<T, R, false, true>(v[t]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) green(col, j + r * NS, v[t][r]);
+        dft<T, R, true, false>(v[t]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm.st_(col, j * R + r, v[t][r]);
+    }
+}
+
+// Forward transform of a tile (stage 0 from src), `green` on the spectrum, and
+// the inverse transform (radices reversed; last stage into dst), in place in sm.
+template <typename T, int R0, int R1, int R2, int JSTEP, bool FIRST_SYNC, class Src, class Sm, class Dst, class Tw,
+          class Green>
+__device__ __forceinline__ void ftransform_green(const Src& src, const Sm& sm, const Dst& dst, int col, int j0,
+                                                 const Tw& TW, const Green& green) {
+    constexpr int N = R0 * R1 * R2;
+    constexpr int B0 = (N / R0) / JSTEP, B1 = (N / R1) / JSTEP, B2 = (N / R2) / JSTEP;
+    static_assert(B0 * JSTEP * R0 == N && B1 * JSTEP * R1 == N, "butterflies must divide evenly");
+    fstage<T, N, R0, 1, B0, JSTEP, 1, false, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{});
+    __syncthreads();
+    if constexpr (R2 == 1) {
+        fstage_green_pivot<T, N, R1, B1, JSTEP>(sm, col, j0, TW, green);
+        __syncthreads();
+        fstage<T, N, R0, R1, B0, JSTEP, 1, true, true>(sm, dst, col, j0, TW, NoPost{});
+    } else {
+        static_assert(B2 * JSTEP * R2 == N, "butterflies must divide evenly");
+        fstage<T, N, R1, R0, B1, JSTEP, 1, false, true>(sm, sm, col, j0, TW, NoPost{});
+        __syncthreads();
+        fstage_green_pivot<T, N, R2, B2, JSTEP>(sm, col, j0, TW, green);
+        __syncthreads();
+        fstage<T, N, R1, R2, B1, JSTEP, 1, true, true>(sm, sm, col, j0, TW, NoPost{});
+        __syncthreads();
+        fstage<T, N, R0, R2 * R1, B0, JSTEP, 1, true, true>(sm, dst, col, j0, TW, NoPost{});
     }
 }
 
@@ -213,11 +294,9 @@ __global__ void __launch_bounds__(NT, min_ctas<NT>()) k_col_fast(FastArgs<T> a) 
             }
             v = scale(v, inv * a.green_scale);
         };
-        ftransform<T, R0, R1, R2, JSTEP, 1, false, false>(g, sm, sm, col, j0, TW, green);
+        ftransform_green<T, R0, R1, R2, JSTEP, false>(g, sm, g, col, j0, TW, green);
         const double bs = block_sum_comp(sum, -comp, red);
         if (threadIdx.x == 0) a.eh_partials[blockIdx.x] = bs;
-        __syncthreads();
-        ftransform<T, R0, R1, R2, JSTEP, 1, true, true>(sm, sm, g, col, j0, TW, NoPost{});
     }
 }
 
@@ -315,9 +394,7 @@ __global__ void __launch_bounds__(NT, 1)
                 }
                 v = scale(v, inv * a.green_scale);
             };
-            ftransform<float, R0, R1, R2, JSTEP, 1, false, true>(sm, sm, sm, col, j0, TW, green);
-            __syncthreads();
-            ftransform<float, R0, R1, R2, JSTEP, 1, true, true>(sm, sm, sm, col, j0, TW, NoPost{});
+            ftransform_green<float, R0, R1, R2, JSTEP, true>(sm, sm, sm, col, j0, TW, green);
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -391,6 +468,169 @@ __global__ void __launch_bounds__(NT, min_ctas<NT>()) k_c2r_fast(T* __restrict__
     ftransform<T, R0, R1, R2, TPL, 2, true, false>(src, sm, dst, 0, j0, TW, NoPost{});
 }
 
+// ------------------------------------------------------------------ bulk-streamed c passes (FP32)
+// Persistent CTAs (two per SM) walk tiles of LINES consecutive lines.  A tile's
+// input is one contiguous block (LINES lines of rho, or LINES rows of the half
+// spectrum with their padding), brought into a ring slot by one bulk copy that
+// completes on the slot's mbarrier; thread 0 keeps NBUF tiles in flight.  The
+// first stage reads the slot, and once every thread has read it (the stage's
+// barrier) thread 0 refills the slot with the tile NBUF ahead, so the next
+// loads overlap this tile's butterflies.  The other stages run in a padded
+// work buffer, and results leave from registers with coalesced stores.  Same
+// arithmetic, in the same order, as k_r2c_fast / k_c2r_fast.
+//
+// Every wait is bounded; after a failed wait thread 0 waits (bounded again)
+// for the copies this CTA still has in flight before the CTA returns.
+template <int NBUF>
+__device__ __forceinline__ void drain_ring(uint64_t* mbar, int k, int ntiles, int* err) {
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i < NBUF; ++i) {
+        const int t = blockIdx.x + (k + i) * gridDim.x;
+        if (t < ntiles) mbar_wait(&mbar[(k + i) % NBUF], (uint32_t)((k + i) / NBUF) & 1u, err);
+    }
+}
+
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF>
+__global__ void __launch_bounds__(NT, 2)
+    k_r2c_stream(const float* __restrict__ rho, FastArgs<float> a, int ntiles, int* err) {
+    constexpr int M = R0 * R1 * R2;
+    constexpr int N = M;
+    constexpr int TPL = NT / LINES;
+    constexpr int LDP = M + M / 16 + 1;
+    constexpr int SLOT = LINES * M;  // complex elements per ring slot
+    constexpr int B0 = (N / R0) / TPL, B1 = (N / R1) / TPL, B2 = (N / R2) / TPL;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cpx<float>* ring = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<float>* S = ring + NBUF * SLOT;
+    TwPair<float>* TW = reinterpret_cast<TwPair<float>*>(S + LINES * LDP);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(TW + 2 * M);
+    for (int k = threadIdx.x; k < 2 * M; k += NT) TW[k] = a.twpc[k];
+    const long long nlines = (long long)a.n1 * a.n2;
+    auto issue = [&](int t, int b) {
+        const long long l0 = (long long)t * LINES;
+        const int nl = (int)min((long long)LINES, nlines - l0);
+        const uint32_t bytes = (uint32_t)nl * M * 8u;
+        mbar_arrive_expect_tx(&mbar[b], bytes);
+        bulk_load(ring + b * SLOT, rho + l0 * 2 * M, bytes, &mbar[b]);
+    };
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&mbar[b], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int b = 0; b < NBUF; ++b) {
+            const int t = blockIdx.x + b * gridDim.x;
+            if (t < ntiles) issue(t, b);
+        }
+    const int l = threadIdx.x / TPL, j0 = threadIdx.x % TPL;
+    LineSmem<float> sm{S + l * LDP};
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        const int b = k % NBUF;
+        const bool ok = mbar_wait(&mbar[b], (uint32_t)(k / NBUF) & 1u, err);
+        if (!__syncthreads_and(ok)) {
+            drain_ring<NBUF>(mbar, k, ntiles, err);
+            break;
+        }
+        const long long gline = (long long)t * LINES + l;
+        const bool act = gline < nlines;
+        LineRealIn<float> src{ring + b * SLOT + l * M, act};
+        auto refill = [&] {
+            const int tn = t + NBUF * gridDim.x;
+            if (threadIdx.x == 0 && tn < ntiles) issue(tn, b);
+        };
+        // M-point transform of z (twiddles exp(-2 pi i e / M) = table entry 2e)
+        fstage<float, N, R0, 1, B0, TPL, 2, false, true>(src, sm, 0, j0, TW, NoPost{}, refill);
+        __syncthreads();
+        if constexpr (R2 == 1) {
+            fstage<float, N, R1, R0, B1, TPL, 2, false, true>(sm, sm, 0, j0, TW, NoPost{});
+        } else {
+            fstage<float, N, R1, R0, B1, TPL, 2, false, true>(sm, sm, 0, j0, TW, NoPost{});
+            __syncthreads();
+            fstage<float, N, R2, R0 * R1, B2, TPL, 2, false, true>(sm, sm, 0, j0, TW, NoPost{});
+        }
+        __syncthreads();
+        // X[k] = E[k] + w^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M
+        if (act) {
+            cpx<float>* out = a.W + gline * a.ldc;
+            for (int kk = j0; kk <= M; kk += TPL) {
+                const cpx<float> z1 = sm.ld_(0, kk == M ? 0 : kk);
+                const cpx<float> z2 = conjg(sm.ld_(0, kk == 0 ? 0 : M - kk));
+                const cpx<float> E = scale(z1 + z2, 0.5f);
+                const cpx<float> d = z1 - z2;
+                const cpx<float> O = mk(d.im * 0.5f, -d.re * 0.5f);
+                out[kk] = E + twmul(O, TW[kk], false);
+            }
+        }
+    }
+}
+
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF>
+__global__ void __launch_bounds__(NT, 2) k_c2r_stream(float* __restrict__ vout, FastArgs<float> a, int ntiles, int* err) {
+    constexpr int M = R0 * R1 * R2;
+    constexpr int N = M;
+    constexpr int TPL = NT / LINES;
+    constexpr int LDP = M + M / 16 + 1;
+    constexpr int B0 = (N / R0) / TPL, B1 = (N / R1) / TPL, B2 = (N / R2) / TPL;
+    const int slot = LINES * a.ldc;  // complex elements per ring slot: LINES padded rows
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cpx<float>* ring = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<float>* S = ring + NBUF * slot;
+    cpx<float>* TWh = S + LINES * LDP;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(TWh + 2 * M);
+    for (int k = threadIdx.x; k < 2 * M; k += NT) TWh[k] = a.twpc[k].h;
+    const TwHi<float> TW{TWh};
+    const long long nlines = (long long)a.n1 * a.n2;
+    auto issue = [&](int t, int b) {
+        const long long l0 = (long long)t * LINES;
+        const int nl = (int)min((long long)LINES, nlines - l0);
+        const uint32_t bytes = (uint32_t)nl * (uint32_t)a.ldc * 8u;
+        mbar_arrive_expect_tx(&mbar[b], bytes);
+        bulk_load(ring + b * slot, a.W + l0 * a.ldc, bytes, &mbar[b]);
+    };
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&mbar[b], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int b = 0; b < NBUF; ++b) {
+            const int t = blockIdx.x + b * gridDim.x;
+            if (t < ntiles) issue(t, b);
+        }
+    const int l = threadIdx.x / TPL, j0 = threadIdx.x % TPL;
+    LineSmem<float> sm{S + l * LDP};
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        const int b = k % NBUF;
+        const bool ok = mbar_wait(&mbar[b], (uint32_t)(k / NBUF) & 1u, err);
+        if (!__syncthreads_and(ok)) {
+            drain_ring<NBUF>(mbar, k, ntiles, err);
+            break;
+        }
+        const long long gline = (long long)t * LINES + l;
+        const bool act = gline < nlines;
+        LineC2RIn<float, TwHi<float>> src{ring + b * slot + l * a.ldc, TW, M, act};
+        LineRealOut<float> dst{reinterpret_cast<cpx<float>*>(vout + (act ? gline : 0) * a.n3), act};
+        auto refill = [&] {
+            const int tn = t + NBUF * gridDim.x;
+            if (threadIdx.x == 0 && tn < ntiles) issue(tn, b);
+        };
+        fstage<float, N, R0, 1, B0, TPL, 2, true, true>(src, sm, 0, j0, TW, NoPost{}, refill);
+        __syncthreads();
+        if constexpr (R2 == 1) {
+            fstage<float, N, R1, R0, B1, TPL, 2, true, true>(sm, dst, 0, j0, TW, NoPost{});
+        } else {
+            fstage<float, N, R1, R0, B1, TPL, 2, true, true>(sm, sm, 0, j0, TW, NoPost{});
+            __syncthreads();
+            fstage<float, N, R2, R0 * R1, B2, TPL, 2, true, true>(sm, dst, 0, j0, TW, NoPost{});
+        }
+    }
+}
+
 // ------------------------------------------------------------------ dispatch
 template <typename T, int COLS, int NT, int R0, int R1, int R2>
 struct ColCfg {
@@ -428,6 +668,52 @@ struct LineCfg {
             k_c2r_fast<T, LINES, NT, R0, R1, R2><<<grid, NT, smem(), s>>>(static_cast<T*>(out), a);
     }
 };
+
+// Bulk-streamed c-pass configuration (FP32): LINES lines per tile, NBUF ring slots, two CTAs per SM.
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF>
+struct LineStreamCfg {
+    static constexpr int lines = LINES, m = R0 * R1 * R2;
+    static size_t smem_work() { return (size_t)LINES * (m + m / 16 + 1) * sizeof(cpx<float>) + NBUF * 8; }
+    static size_t smem_r2c() {
+        return (size_t)NBUF * LINES * m * sizeof(cpx<float>) + smem_work() + (size_t)2 * m * sizeof(TwPair<float>);
+    }
+    static size_t smem_c2r(int ldc) {
+        return (size_t)NBUF * LINES * ldc * sizeof(cpx<float>) + smem_work() + (size_t)2 * m * sizeof(cpx<float>);
+    }
+    static size_t smem() { return 0; }  // checked per kernel in configure()
+    static cudaError_t configure(int optin) {
+        cudaError_t e;
+        if ((e = allow_max_dynamic_smem(k_r2c_stream<LINES, NT, R0, R1, R2, NBUF>, optin))) return e;
+        return allow_max_dynamic_smem(k_c2r_stream<LINES, NT, R0, R1, R2, NBUF>, optin);
+    }
+    static long long launch(bool inverse, int sm_count, const void* in, void* out, const FastArgs<float>& a,
+                            int* err, cudaStream_t s) {
+        const long long nlines = (long long)a.n1 * a.n2;
+        const int ntiles = (int)((nlines + LINES - 1) / LINES);
+        // two CTAs per SM where both fit in the SM's 228 KB of shared memory (1 KB reserved per CTA)
+        const size_t need = inverse ? smem_c2r(a.ldc) : smem_r2c();
+        int grid = (2 * (need + 1024) <= 228 * 1024 ? 2 : 1) * sm_count;
+        if (grid > ntiles) grid = ntiles;
+        if (!inverse)
+            k_r2c_stream<LINES, NT, R0, R1, R2, NBUF>
+                <<<grid, NT, smem_r2c(), s>>>(static_cast<const float*>(in), a, ntiles, err);
+        else
+            k_c2r_stream<LINES, NT, R0, R1, R2, NBUF>
+                <<<grid, NT, smem_c2r(a.ldc), s>>>(static_cast<float*>(out), a, ntiles, err);
+        return grid;
+    }
+};
+
+// Streamed c passes by M = N3 / 2 (tiles of 32 KB of rho).
+template <class F>
+bool with_line_stream_cfg(int m, F&& f) {
+    switch (m) {
+        case 128: f(LineStreamCfg<32, 256, 16, 8, 1, 2>{}); return true;
+        case 256: f(LineStreamCfg<16, 256, 16, 16, 1, 2>{}); return true;
+        case 512: f(LineStreamCfg<8, 256, 8, 8, 8, 2>{}); return true;
+        default: return false;
+    }
+}
 
 // TMA-streamed column pass configuration (FP32): 16 columns (128-byte rows) per tile.
 template <int NT, int R0, int R1, int R2, int NBUF>
@@ -527,6 +813,13 @@ bool with_line_cfg(int m, int variant, F&& f) {
 }
 int line_variants(int m) { return (m == 128 || m == 256 || m == 512) ? 2 : 1; }
 
+// Variant line_variants(M) of the c passes: the bulk-streamed kernels (FP32; the plan's
+// row stride and the caller's grid pointers must allow 16-byte bulk copies).
+bool line_stream_available(const Plan& p) {
+    return p.prec != HARTREE_FP64 && p.d_err != nullptr && p.sm_count > 0 && (p.ldc * 8) % 16 == 0 &&
+           with_line_stream_cfg(p.M, [](auto) {});
+}
+
 template <typename T>
 FastArgs<T> make_fast_args(const Plan& p) {
     FastArgs<T> a;
@@ -576,6 +869,14 @@ cudaError_t configure_fast_t(const Plan& p, int optin) {
         if (e == cudaSuccess) e = c.configure(optin);
     };
     for (int v = 0; v < line_variants(p.M); ++v) with_line_cfg<T>(p.M, v, cfg);
+    if constexpr (sizeof(T) == 4) {
+        if (line_stream_available(p))
+            with_line_stream_cfg(p.M, [&](auto c) {
+                const size_t need = std::max(c.smem_r2c(), c.smem_c2r(p.ldc));
+                if (e == cudaSuccess && need + 2048 > (size_t)optin) e = cudaErrorInvalidConfiguration;
+                if (e == cudaSuccess) e = c.configure(optin);
+            });
+    }
     for (int v = 0; v < col_variants(p.n[1]); ++v) with_col_cfg<T>(p.n[1], v, cfg);
     for (int v = 0; v < col_variants(p.n[0]); ++v) with_col_cfg<T>(p.n[0], v, cfg);
     if constexpr (sizeof(T) == 4) {
@@ -600,7 +901,18 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
     FastArgs<T> a = make_fast_args<T>(p);
     long long grid = -1;
     if (pass == 0 || pass == 4) {
-        with_line_cfg<T>(p.M, p.var[0], [&](auto c) {
+        if constexpr (sizeof(T) == 4) {
+            const void* grid_ptr = pass == 0 ? rho : vh;
+            if (p.var[0] == line_variants(p.M) && line_stream_available(p) &&
+                reinterpret_cast<uintptr_t>(grid_ptr) % 16 == 0) {
+                with_line_stream_cfg(p.M, [&](auto c) {
+                    grid = c.launch(pass == 4, p.sm_count, rho, vh, a, p.d_err, s);
+                });
+                return grid;
+            }
+        }
+        const int lv = p.var[0] < line_variants(p.M) ? p.var[0] : 0;  // misaligned grid: plain kernel
+        with_line_cfg<T>(p.M, lv, [&](auto c) {
             grid = ((long long)p.n[0] * p.n[1] + c.lines - 1) / c.lines;
             c.launch(pass == 4, (unsigned)grid, rho, vh, a, s);
         });
@@ -635,7 +947,7 @@ long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, c
 }
 
 int fast_variants(const Plan& p, int kind) {
-    if (kind == 0) return (p.use_fast & 1) ? line_variants(p.M) : 1;
+    if (kind == 0) return (p.use_fast & 1) ? line_variants(p.M) + (line_stream_available(p) ? 1 : 0) : 1;
     const int ax = kind == 1 ? 1 : 0;
     if (!(p.use_fast & (kind == 1 ? 2 : 4))) return 1;
     return col_variants(p.n[ax]) + (col_tma_available(p, ax) ? col_tma_variants(p.n[ax]) : 0);

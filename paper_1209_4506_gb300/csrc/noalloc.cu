@@ -105,6 +105,10 @@ extern "C" int hartree_solve_density_noalloc(const hartree_desc* desc, const voi
     }
     if (d.n[2] % 2 != 0 || d.n[2] < 4)
         return noalloc_fail(HARTREE_ERR_UNSUPPORTED_SIZE, "solve_density_noalloc: N3 must be even and >= 4");
+    const uintptr_t pair = d.precision == HARTREE_FP64 ? 16 : 8;  // grid lines move as (re, im) pairs
+    if (reinterpret_cast<uintptr_t>(rho) % pair != 0 || reinterpret_cast<uintptr_t>(vh) % pair != 0)
+        return noalloc_fail(HARTREE_ERR_INVALID, pair == 16 ? "solve_density_noalloc: grids must be aligned to 16 bytes"
+                                                            : "solve_density_noalloc: grids must be aligned to 8 bytes");
 
     Plan p;
     p.desc = d;

@@ -277,9 +277,10 @@ def test_single_passes_reproduce_solve_density(precision):
 def test_kernel_variants_give_identical_potential(shape, precision):
     """Every compiled tile shape and radix order (and the TMA-streamed passes) computes V_H within tolerance.
 
-    Variants 0..2 keep the radix order of the plain kernels (tile shapes and the
-    TMA stream differ only in which thread does a butterfly), so their V_H is
-    bit-identical; the radix-32 TMA variants (3, 4) round differently."""
+    b / a variants 0..2 keep the radix order of the plain kernels (tile shapes and
+    the TMA stream differ only in which thread does a butterfly), so with c
+    variants 0 and 1 their V_H is bit-identical; the radix-32 TMA variants (3, 4)
+    round differently, and so may the streamed inverse c pass (c variant 2)."""
     import itertools
 
     from paper_1209_4506_gb300 import capi
@@ -304,15 +305,81 @@ def test_kernel_variants_give_identical_potential(shape, precision):
     for choice, vh, eh in results:
         assert rel_l2(vh.double().cpu().numpy(), v_ref) <= TOL[precision]["v"], choice
         assert abs(eh - e_ref) <= WHITE_NOISE_E_TOL[precision] * abs(e_ref), choice
-        if max(choice) <= 2:
-            assert torch.equal(vh, results[0][1]), choice
-            # E_H: same terms, different grouping (per-CTA partials, persistent CTAs sum across tiles)
+        if max(choice[1:]) <= 2:
+            # E_H is formed before the inverse c pass, from the same terms in a different grouping
+            # (per-CTA partials; persistent CTAs sum across tiles)
             assert abs(eh - results[0][2]) <= 1e-10 * abs(results[0][2]), choice
+        if choice[0] <= 1 and max(choice[1:]) <= 2:
+            assert torch.equal(vh, results[0][1]), choice
     picks = plan.autotune()
     plan.device_status()
     assert all(0 <= p <= 4 for p in picks)
     with pytest.raises(capi.HartreeError):
         plan.set_variants([0, 0, 5])
+
+
+@pytest.mark.parametrize(
+    "shape,cell",
+    [((5, 9, 256), (1.0, 1.3, 30.0)),  # M = 128: 45 lines, tiles of 32 (ragged last tile of 13)
+     ((3, 10, 512), (0.8, 2.0, 60.0)),  # M = 256: 30 lines, tiles of 16 (last tile 14 lines)
+     ((3, 5, 1024), (0.7, 1.0, 110.0)),  # M = 512: 15 lines, tiles of 8
+     ((512, 64, 512), (60.0, 8.0, 60.0))],  # 2,048 tiles: every ring slot reused many times
+)
+def test_streamed_c_passes_equal_plain_kernels(shape, cell):
+    """The bulk-streamed c passes (variant 2 of pass kind 0) match the plain kernels.
+
+    The forward pass does the same arithmetic in the same order, so E_H (formed
+    from its output) is bit-identical; the inverse pass may contract its products
+    into FMAs differently, so V_H agrees to FP32 rounding.  A grid pointer that
+    is not 16-byte aligned cannot be bulk-copied: the call then takes the plain
+    kernel, with the same V_H bit for bit."""
+    rng = np.random.default_rng(sum(shape) + 7)
+    rho32 = rng.standard_normal(shape).astype(np.float32)
+    v_ref, e_ref, _, _ = O.poisson(cell, rho32.astype(np.float64))
+    plan = HartreePlan(shape, cell, 0.5, "fp32")
+    rho = torch.tensor(rho32, device="cuda")
+    plan.set_variants([0, 0, 0])
+    v0, e0 = plan.solve_density(rho)
+    plan.set_variants([2, 0, 0])
+    v2, e2 = plan.solve_density(rho)
+    torch.cuda.synchronize()
+    plan.device_status()
+    assert rel_l2(v2.double().cpu().numpy(), v0.double().cpu().numpy()) <= 1e-6
+    assert e0.item() == e2.item()
+    assert rel_l2(v2.double().cpu().numpy(), v_ref) <= TOL["fp32"]["v"]
+    assert abs(e2.item() - e_ref) <= WHITE_NOISE_E_TOL["fp32"] * abs(e_ref)
+    # grids 8- but not 16-byte aligned (offset by two floats): the plain kernels run instead
+    buf_in = torch.empty(rho.numel() + 2, dtype=torch.float32, device="cuda")
+    buf_out = torch.empty(rho.numel() + 2, dtype=torch.float32, device="cuda")
+    r_mis = buf_in[2:].view(shape)
+    r_mis.copy_(rho)
+    v_mis = buf_out[2:].view(shape)
+    plan.solve_density(r_mis, vh=v_mis)
+    torch.cuda.synchronize()
+    plan.device_status()
+    assert torch.equal(v_mis, v0)
+    plan.close()
+
+
+def test_grids_off_the_pair_alignment_are_rejected():
+    """Grid lines move as (re, im) pairs: a grid not aligned to twice the element size is
+    refused on the host (HARTREE_ERR_INVALID) before any kernel is launched."""
+    from paper_1209_4506_gb300 import capi
+
+    shape, cell = (8, 8, 16), (2.0, 2.0, 4.0)
+    for precision, dt, off in (("fp32", torch.float32, 1), ("fp64", torch.float64, 1)):
+        plan = HartreePlan(shape, cell, 0.5, precision)
+        buf = torch.zeros(int(np.prod(shape)) + off, dtype=dt, device="cuda")
+        good = torch.zeros(shape, dtype=dt, device="cuda")
+        bad = buf[off:].view(shape)
+        with pytest.raises(capi.HartreeError) as ei:
+            plan.solve_density(bad, vh=good)
+        assert ei.value.status == capi.HARTREE_ERR_INVALID
+        with pytest.raises(capi.HartreeError):
+            plan.solve_density(good, vh=bad)
+        with pytest.raises(capi.HartreeError):
+            plan.solve_pass(0, rho=bad, vh=good)
+        plan.close()
 
 
 def test_autotune_cache_roundtrip(tmp_path):
