@@ -9,21 +9,21 @@
 // box (structure A of Sec. 3.2.2): box point m of axis d is the unwrapped grid
 // index lo_d + m at offset d_m = (lo_d + m) h_d - X_d, and
 //   fac[m] = exp(-d_m^2/s^2),  dfac[m] = d_m exp(-d_m^2/s^2).
-// k_atom_prep finds the box; k_atom_factors fills the arrays once per call in
-// FP64 (three exponentials per run of 8 box points, then the exact ratio
-// recurrence f_{m+1} = f_m r_m, r_{m+1} = r_m exp(-2 h^2/s^2)) and rounds each
-// value once, so the FP32 splat and gather carry no exponential rounding bias.
+// k_leaf_setup runs one CTA per leaf of `apl` consecutive atoms: it finds each
+// atom's box and fills its factor arrays once per call in FP64 (three
+// exponentials per run of 8 box points, then the exact ratio recurrence
+// f_{m+1} = f_m r_m, r_{m+1} = r_m exp(-2 h^2/s^2)), rounding each value once,
+// so the FP32 splat and gather carry no exponential rounding bias.  It then
+// builds the leaf's box (structure C of Sec. 3.2.2: the parallelepiped around
+// the basis spheres of the atoms one process holds) and lists each atom in every
+// splat tile its box reaches.  In the order of the modified recursive bisection
+// (Sec. 3.1) a leaf is a compact cluster, so a tile meets a few leaves, i.e. a
+// few contiguous atom ranges.
 //
-// k_leaf_boxes builds, for each leaf of `apl` consecutive atoms, the integer
-// box covering its atoms (structure C of Sec. 3.2.2: the parallelepiped
-// around the basis spheres of the atoms one process holds).  In the order of
-// the modified recursive bisection (Sec. 3.1) a leaf is a compact cluster, so
-// a grid tile meets a few leaves, i.e. a few contiguous atom ranges.
-//
-// k_splat is a gather: each CTA owns a 16 x 8 x 32 grid tile, selects the
-// leaves and then the atoms whose boxes reach it (integer tests, ordered
-// compaction so the summation order is fixed), stages their factors and adds
-// q n fa fb fc with one FMA per grid point and atom.
+// k_splat_binned is a gather: each CTA owns a 16 x 8 x 32 grid tile, takes the
+// atoms listed for it in increasing index (or selects them from the leaf boxes
+// when the list overflowed), stages their factors and adds q n fa fb fc with
+// one FMA per grid point and atom.
 //
 // k_forces walks one atom's box (or a slab of it) per CTA: each thread owns
 // fixed (b, c) points with their weights in registers and streams over the a
@@ -32,6 +32,7 @@
 // use compensated working-precision accumulators and one FP64 block
 // reduction.  Per (atom, slab) partials are reduced in a fixed order.
 #include <algorithm>
+#include <climits>
 
 #include "atoms_dev.cuh"
 #include "tma.cuh"
@@ -40,26 +41,6 @@ namespace hartree {
 
 namespace {
 
-template <typename T>
-__global__ void k_atom_prep(AtomArgs<T> a) {
-    atom_prep_one(a, blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-template <typename T>
-__global__ void k_atom_factors(AtomArgs<T> a) {
-    atom_factors_one(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-template <typename T>
-__global__ void k_leaf_boxes(const AtomPrep<T>* __restrict__ prep, int n, int apl, int nleaves, int n1, int n2,
-                             int n3, int* __restrict__ leaf) {
-    leaf_box_one(prep, n, apl, nleaves, n1, n2, n3, leaf, blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_splat(AtomArgs<T> a, T* __restrict__ rho, int tiles_b, int tiles_c) {
-    splat_tile(a, rho, tiles_b, tiles_c, blockIdx.x);
-}
 // ---------------------------------------------------------------- tile binning
 // The tiles along one axis that hold at least one wrapped index of the box
 // [lo, lo + cnt): count of them, and tile(k) for k < count.
@@ -82,103 +63,89 @@ __device__ __forceinline__ AxisTiles axis_tiles(int lo, int cnt, int n, int T, i
     return {t0, nT - t0, nT - t0 + t2 + 1};
 }
 
-// One warp per atom enumerates the tiles its box reaches.  FILL = false counts
-// atoms per tile; FILL = true appends the atom to each tile's list (order fixed
-// later by the splat, which sorts each list).
-template <typename T, bool FILL>
-__global__ void k_bin(AtomArgs<T> a, int tA, int tB, int tC, int* __restrict__ count, const int* __restrict__ off,
-                      int* __restrict__ cursor, int* __restrict__ list) {
-    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= a.n) return;
-    const AtomPrep<T>& p = a.prep[i];
-    const AxisTiles ra = axis_tiles(p.lo[0], p.cnt[0], a.n1, TA, tA);
-    const AxisTiles rb = axis_tiles(p.lo[1], p.cnt[1], a.n2, TB, tB);
-    const AxisTiles rc = axis_tiles(p.lo[2], p.cnt[2], a.n3, TC, tC);
-    const int nbc = rb.count * rc.count;
-    const int tot = ra.count * nbc;
-    for (int k = lane; k < tot; k += 32) {
-        const int ka = k / nbc, r = k - ka * nbc, kb = r / rc.count, kc = r - kb * rc.count;
-        const int tile = (ra.tile(ka) * tB + rb.tile(kb)) * tC + rc.tile(kc);
-        if (FILL)
-            list[off[tile] + atomicAdd(cursor + tile, 1)] = i;
-        else
-            atomicAdd(count + tile, 1);
+// One CTA per leaf (apl consecutive atoms in bisection order): the atoms' boxes
+// and factor arrays; the leaf's box (structure C of Sec. 3.2.2: the box around
+// the cutoff boxes of the leaf's atoms, each shifted to the periodic image
+// nearest the leaf's first atom); and, with `bins`, each atom appended to the
+// list of every splat tile its box reaches.  A list entry carries the atom's
+// wrapped box start and length per axis, so the splat reads the factors with no
+// further lookup.  Slots are taken with atomics, so a list is unordered (the
+// splat sorts it); a tile reached by more than kBinCap atoms keeps counting and
+// the splat then selects its atoms from the leaf boxes instead.
+template <typename T>
+__global__ void __launch_bounds__(128) k_leaf_setup(AtomArgs<T> a, int tA, int tB, int tC, int* __restrict__ cursor,
+                                                   int4* __restrict__ list, bool bins) {
+    __shared__ int bmin[3], bmax[3];
+    const int l = blockIdx.x;
+    const int i0 = l * a.apl, i1 = min(a.n, i0 + a.apl);
+    for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) atom_prep_one(a, i);
+    if (threadIdx.x < 3) {
+        bmin[threadIdx.x] = INT_MAX;
+        bmax[threadIdx.x] = INT_MIN;
+    }
+    __syncthreads();  // the boxes are visible to the whole CTA
+    const int runs = (a.fb + kRun - 1) / kRun;
+    const int ntask = (i1 - i0) * 3 * runs;
+    for (int t = threadIdx.x; t < ntask; t += blockDim.x) atom_factors_one(a, (long long)i0 * 3 * runs + t);
+    if (!bins) return;
+    const int ns[3] = {a.n1, a.n2, a.n3};
+    for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x)
+        for (int d = 0; d < 3; ++d) {
+            int lo = a.prep[i].lo[d];
+            const int x = lo - a.prep[i0].lo[d] + ns[d] / 2;
+            const int k = x >= 0 ? x / ns[d] : -((-x + ns[d] - 1) / ns[d]);  // floor(x / n)
+            lo -= k * ns[d];
+            atomicMin(&bmin[d], lo);
+            atomicMax(&bmax[d], lo + a.prep[i].cnt[d]);
+        }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        a.leaf[6 * l + d] = bmin[d];
+        a.leaf[6 * l + 3 + d] = min(bmax[d] - bmin[d], ns[d]);
+    }
+    for (int i = i0; i < i1; ++i) {
+        const AtomPrep<T> p = a.prep[i];
+        const AxisTiles ra = axis_tiles(p.lo[0], p.cnt[0], a.n1, TA, tA);
+        const AxisTiles rb = axis_tiles(p.lo[1], p.cnt[1], a.n2, TB, tB);
+        const AxisTiles rc = axis_tiles(p.lo[2], p.cnt[2], a.n3, TC, tC);
+        const int nbc = rb.count * rc.count;
+        const int tot = ra.count * nbc;
+        const int4 entry = make_int4(i, p.st[0] | (p.cnt[0] << 16), p.st[1] | (p.cnt[1] << 16),
+                                     p.st[2] | (p.cnt[2] << 16));
+        for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+            const int ka = k / nbc, r = k - ka * nbc, kb = r / rc.count, kc = r - kb * rc.count;
+            const int tile = (ra.tile(ka) * tB + rb.tile(kb)) * tC + rc.tile(kc);
+            const int slot = atomicAdd(cursor + tile, 1);
+            if (slot < kBinCap) list[(long long)tile * kBinCap + slot] = entry;
+        }
     }
 }
-
-// Exclusive prefix sum of the per-tile counts (one CTA of 1024 threads, in
-// chunks of 4096 counts with a running carry); also clears the fill cursors.
-// off[n_tiles] is the total.
-__global__ void __launch_bounds__(1024) k_bin_scan(const int* __restrict__ count, int n_tiles, int* __restrict__ off,
-                                                   int* __restrict__ cursor) {
-    __shared__ int warp_tot[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int carry = 0;
-    for (int base = 0; base < n_tiles; base += 4096) {
-        const int t0 = base + 4 * threadIdx.x;
-        int v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = t0 + k < n_tiles ? count[t0 + k] : 0;
-        const int sum = v[0] + v[1] + v[2] + v[3];
-        int incl = sum;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) warp_tot[w] = incl;
-        __syncthreads();
-        if (w == 0) {
-            int x = warp_tot[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            warp_tot[lane] = x;  // inclusive over warps
-        }
-        __syncthreads();
-        int run = carry + incl - sum + (w > 0 ? warp_tot[w - 1] : 0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (t0 + k < n_tiles) {
-                off[t0 + k] = run;
-                cursor[t0 + k] = 0;
-                run += v[k];
-            }
-        carry += warp_tot[31];
-        __syncthreads();  // warp_tot is rewritten by the next chunk
-    }
-    if (threadIdx.x == 0) off[n_tiles] = carry;
-}
-
-constexpr int kBinCap = 1024;  // longest tile list the binned splat sorts in shared memory
 
 // Splat of one tile from its bin: the list is sorted by atom index in shared
 // memory (a rank sort; indices in a list are distinct), so the summation order
-// is the same as that of the leaf-selecting splat, then factors are staged in
-// batches and accumulated as there.  Longer lists take the leaf-selecting path.
+// is that of the leaf-selecting splat, then factors are staged in batches and
+// accumulated as there.  Longer lists take the leaf-selecting path.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_splat_binned(AtomArgs<T> a, T* __restrict__ rho, int tiles_b,
-                                                           int tiles_c, const int* __restrict__ count,
-                                                           const int* __restrict__ off,
-                                                           const int* __restrict__ list) {
-    __shared__ int ids[kBinCap];
-    __shared__ int sorted[kBinCap];
+                                                           int tiles_c, const int* __restrict__ cursor,
+                                                           const int4* __restrict__ list) {
+    __shared__ int4 ent[kBinCap];
+    __shared__ int4 sorted[kBinCap];
     __shared__ __align__(16) T fa[kBatch][TA];
     __shared__ T fb[kBatch][TB], fc[kBatch][TC];
     const int tile = blockIdx.x;
-    const int L = count[tile];
+    const int L = cursor[tile];
     if (L > kBinCap) {
         splat_tile(a, rho, tiles_b, tiles_c, tile);
         return;
     }
-    const int base = off[tile];
-    for (int e = threadIdx.x; e < L; e += kThreads) ids[e] = list[base + e];
+    for (int e = threadIdx.x; e < L; e += kThreads) ent[e] = list[(long long)tile * kBinCap + e];
     __syncthreads();
     for (int e = threadIdx.x; e < L; e += kThreads) {
-        const int v = ids[e];
+        const int4 v = ent[e];
         int r = 0;
-        for (int f = 0; f < L; ++f) r += ids[f] < v;
+        for (int f = 0; f < L; ++f) r += ent[f].x < v.x;
         sorted[r] = v;
     }
     const int ta = tile / (tiles_b * tiles_c);
@@ -192,7 +159,30 @@ __global__ void __launch_bounds__(kThreads) k_splat_binned(AtomArgs<T> a, T* __r
     for (int bb = 0; bb < L; bb += kBatch) {
         const int nb = min(kBatch, L - bb);
         __syncthreads();  // sorted[] complete / previous batch consumed
-        stage_factors(a, sorted + bb, nb, a0, b0, c0, fa, fb, fc);
+        // factors: one global load per staged value (the entry carries the box), plus q n per c value
+        for (int e = threadIdx.x; e < nb * TC; e += kThreads) {
+            const int t = e / TC, k = e - t * TC;
+            const int4 E = sorted[bb + t];
+            const T sc = c0 + k < a.n3 ? image_sum(a.fac + ((long long)E.x * 3 + 2) * a.fb, c0 + k, E.w & 0xffff,
+                                                   E.w >> 16, a.n3)
+                                       : T(0);
+            const AtomPrep<T>& p = a.prep[E.x];
+            fc[t][k] = p.qn * sc + p.ql * sc;
+        }
+        for (int e = threadIdx.x; e < nb * TA; e += kThreads) {
+            const int t = e / TA, f = e - t * TA;
+            const int4 E = sorted[bb + t];
+            fa[t][f] = a0 + f < a.n1
+                           ? image_sum(a.fac + (long long)E.x * 3 * a.fb, a0 + f, E.y & 0xffff, E.y >> 16, a.n1)
+                           : T(0);
+        }
+        for (int e = threadIdx.x; e < nb * TB; e += kThreads) {
+            const int t = e / TB, f = e - t * TB;
+            const int4 E = sorted[bb + t];
+            fb[t][f] = b0 + f < a.n2 ? image_sum(a.fac + ((long long)E.x * 3 + 1) * a.fb, b0 + f, E.z & 0xffff,
+                                                 E.z >> 16, a.n2)
+                                     : T(0);
+        }
         __syncthreads();
         for (int t = 0; t < nb; ++t) {
             const T s = fb[t][warp] * fc[t][lane];
@@ -442,59 +432,29 @@ __global__ void k_forces_finalize(const double* __restrict__ part, int n, int sl
 }
 
 
+// Per-atom boxes and factor arrays (one CTA per leaf); with `bins`, also the leaf
+// boxes and the atom lists of the splat tiles.
 template <typename T>
-cudaError_t prep_atoms(const Plan& p, const AtomArgs<T>& a, cudaStream_t s) {
-    if (a.n == 0) return cudaSuccess;
-    p.launches += 2;
-    k_atom_prep<T><<<(a.n + 127) / 128, 128, 0, s>>>(a);
-    const long long nt = 3LL * a.n * ((a.fb + kRun - 1) / kRun);
-    k_atom_factors<T><<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t splat_prepared(const Plan& p, const AtomArgs<T>& a, void* rho, cudaStream_t s) {
-    if (p.use_bins) {
-        const int tA = p.tiles[0], tB = p.tiles[1], tC = p.tiles[2];
-        cudaError_t e = cudaSuccess;
-        if (a.n > 0) {
-            // leaf boxes too: a tile whose list is longer than the sort capacity selects from them
-            p.launches += 4;
-            k_leaf_boxes<T><<<(a.nleaves + 127) / 128, 128, 0, s>>>(a.prep, a.n, p.apl, a.nleaves, p.n[0], p.n[1],
-                                                                    p.n[2], p.leaf_box);
-            e = cudaMemsetAsync(p.bin_count, 0, sizeof(int) * p.n_tiles, s);
-            if (e != cudaSuccess) return e;
-            const unsigned nb = (unsigned)(((long long)a.n * 32 + 255) / 256);
-            k_bin<T, false><<<nb, 256, 0, s>>>(a, tA, tB, tC, p.bin_count, p.bin_off, p.bin_cursor, p.bin_list);
-            k_bin_scan<<<1, 1024, 0, s>>>(p.bin_count, p.n_tiles, p.bin_off, p.bin_cursor);
-            k_bin<T, true><<<nb, 256, 0, s>>>(a, tA, tB, tC, p.bin_count, p.bin_off, p.bin_cursor, p.bin_list);
-        } else {
-            e = cudaMemsetAsync(p.bin_count, 0, sizeof(int) * p.n_tiles, s);
-            if (e != cudaSuccess) return e;
-        }
-        p.launches += 1;
-        k_splat_binned<T><<<(unsigned)p.n_tiles, kThreads, 0, s>>>(a, static_cast<T*>(rho), tB, tC, p.bin_count,
-                                                                      p.bin_off, p.bin_list);
-        return cudaGetLastError();
-    }
-    p.launches += (a.nleaves > 0 ? 1 : 0) + 1;
-    if (a.nleaves > 0)
-        k_leaf_boxes<T><<<(a.nleaves + 127) / 128, 128, 0, s>>>(a.prep, a.n, p.apl, a.nleaves, p.n[0], p.n[1],
-                                                                p.n[2], p.leaf_box);
-    const int tA = (p.n[0] + TA - 1) / TA, tB = (p.n[1] + TB - 1) / TB, tC = (p.n[2] + TC - 1) / TC;
-    k_splat<T><<<(unsigned)tA * tB * tC, kThreads, 0, s>>>(a, static_cast<T*>(rho), tB, tC);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t splat_impl(const Plan& p, const double* pos, const double* q, int n, void* rho, bool prepared,
-                       cudaStream_t s) {
-    AtomArgs<T> a = make_atom_args<T>(p, pos, q, n);
-    if (!prepared) {
-        cudaError_t e = prep_atoms<T>(p, a, s);
+cudaError_t prep_atoms(const Plan& p, const AtomArgs<T>& a, bool bins, cudaStream_t s) {
+    if (bins) {
+        cudaError_t e = cudaMemsetAsync(p.bin_cursor, 0, sizeof(int) * (size_t)p.n_tiles, s);
         if (e != cudaSuccess) return e;
     }
-    return splat_prepared<T>(p, a, rho, s);
+    if (a.n == 0) return cudaSuccess;
+    p.launches += 1;
+    k_leaf_setup<T><<<a.nleaves, 128, 0, s>>>(a, p.tiles[0], p.tiles[1], p.tiles[2], p.bin_cursor, p.bin_list, bins);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t splat_impl(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s) {
+    AtomArgs<T> a = make_atom_args<T>(p, pos, q, n);
+    cudaError_t e = prep_atoms<T>(p, a, true, s);
+    if (e != cudaSuccess) return e;
+    p.launches += 1;
+    k_splat_binned<T><<<(unsigned)p.n_tiles, kThreads, 0, s>>>(a, static_cast<T*>(rho), p.tiles[1], p.tiles[2],
+                                                                  p.bin_cursor, p.bin_list);
+    return cudaGetLastError();
 }
 
 size_t forces_smem(const Plan& p, size_t real_size, int vw, int kp);
@@ -551,7 +511,7 @@ cudaError_t forces_impl(const Plan& p, const double* pos, const double* q, int n
     if (n == 0) return cudaSuccess;
     AtomArgs<T> a = make_atom_args<T>(p, pos, q, n);
     if (!prepared) {
-        cudaError_t e = prep_atoms<T>(p, a, s);
+        cudaError_t e = prep_atoms<T>(p, a, false, s);
         if (e != cudaSuccess) return e;
     }
     p.launches += 2;
@@ -593,10 +553,8 @@ cudaError_t configure_atom_kernels(const Plan& p) {
     return p.prec == HARTREE_FP64 ? configure_atoms<double>(optin) : configure_atoms<float>(optin);
 }
 
-cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s,
-                         bool prepared) {
-    return p.prec == HARTREE_FP64 ? splat_impl<double>(p, pos, q, n, rho, prepared, s)
-                                  : splat_impl<float>(p, pos, q, n, rho, prepared, s);
+cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s) {
+    return p.prec == HARTREE_FP64 ? splat_impl<double>(p, pos, q, n, rho, s) : splat_impl<float>(p, pos, q, n, rho, s);
 }
 
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,

@@ -133,7 +133,7 @@ void free_plan(Plan& p) {
     void* ptrs[] = {p.W,           p.R,        p.tw[0],         p.tw[1], p.tw[2], p.twp[0], p.twp[1], p.twp[2], p.gsq[0],
                     p.gsq[1],      p.gsq[2],   p.eh_partials,   p.leaf_box,
                     p.atom_prep,   p.atom_fac, p.atom_dfac, p.force_partials, p.d_pos,   p.d_q,   p.d_f,   p.d_eh,
-                    p.d_err,       p.bin_count, p.bin_off, p.bin_cursor, p.bin_list, p.tc_dft};
+                    p.d_err,       p.bin_cursor, p.bin_list, p.tc_dft};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -247,22 +247,12 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
     p.use_fast = fast_pass_mask(p);
     p.max_force_slabs = 1216;
 
-    // tile bins: an atom's box of at most box_max points meets at most box_max / T + 3 tiles along an axis
-    // (two wrapped segments, a partial last tile); the list is skipped when that bound is too large
     {
         const int T[3] = {TA, TB, TC};
-        long long per_atom = 1;
-        for (int i = 0; i < 3; ++i) {
-            p.tiles[i] = (p.n[i] + T[i] - 1) / T[i];
-            per_atom *= std::min(p.tiles[i], p.box_max / T[i] + 3);
-        }
+        for (int i = 0; i < 3; ++i) p.tiles[i] = (p.n[i] + T[i] - 1) / T[i];
         p.n_tiles = p.tiles[0] * p.tiles[1] * p.tiles[2];
-        p.bin_cap = per_atom * p.max_atoms;
-        p.use_bins = p.bin_cap <= (1LL << 26);  // at most 256 MB of list
-        if (!p.use_bins) p.bin_cap = 0;
     }
     const size_t ntot = (size_t)p.n[0] * p.n[1] * p.n[2];
-    const size_t nbin = p.use_bins ? (size_t)p.n_tiles : 0;
     struct Alloc {
         void** ptr;
         size_t bytes;
@@ -289,10 +279,8 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         {(void**)&p.d_f, (size_t)p.max_atoms * 3 * sizeof(double)},
         {(void**)&p.d_eh, sizeof(double)},
         {(void**)&p.d_err, sizeof(int)},
-        {(void**)&p.bin_count, (nbin + 1) * sizeof(int)},
-        {(void**)&p.bin_off, (nbin + 1) * sizeof(int)},
-        {(void**)&p.bin_cursor, (nbin + 1) * sizeof(int)},
-        {(void**)&p.bin_list, ((size_t)p.bin_cap + 1) * sizeof(int)},
+        {(void**)&p.bin_cursor, (size_t)p.n_tiles * sizeof(int)},
+        {(void**)&p.bin_list, (size_t)p.n_tiles * kBinCap * sizeof(int4)},
         {&p.tc_dft, p.prec == HARTREE_FP32_TC_SPLIT ? tc_table_bytes() : 16},
     };
     for (auto& a : allocs) {
@@ -383,12 +371,14 @@ int hartree_forces(hartree_plan plan, const double* pos, const double* q, int n,
         return fail(HARTREE_ERR_INVALID, "forces: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
-    if (!vh) {
+    const bool recompute = vh == nullptr;
+    if (recompute) {
         e = launch_splat(plan->p, pos, q, n, plan->p.R, s);
         if (e == cudaSuccess) e = launch_poisson(plan->p, plan->p.R, plan->p.R, nullptr, s);
         vh = plan->p.R;
     }
-    if (e == cudaSuccess) e = launch_forces(plan->p, pos, q, n, vh, f, phi, s);
+    // the splat of a recompute already prepared the atoms' boxes and factors
+    if (e == cudaSuccess) e = launch_forces(plan->p, pos, q, n, vh, f, phi, s, recompute);
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "forces");
 }
 

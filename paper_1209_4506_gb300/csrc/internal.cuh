@@ -16,6 +16,7 @@ constexpr int kThreads = 256;
 constexpr int TA = 16, TB = 8, TC = 32;  // splat tile (a, b, c)
 constexpr int kMaxAxis = 4096;       // largest grid size along one axis
 constexpr int kMaxBoxPoints = 1024;  // largest per-axis extent of one atom's cutoff box (points)
+constexpr int kBinCap = 64;          // atoms listed per splat tile; a fuller tile selects from the leaf boxes
 
 // Arguments of the five Poisson passes (one precision).
 template <typename T>
@@ -183,15 +184,11 @@ struct Plan {
     bool tma_ok = false;      // tensor maps over W are valid
     CUtensorMap tmap_b, tmap_a;  // bit 0: c passes, bit 1: b passes, bit 2: a pass use the specialised kernels
     size_t smem_c, smem_b, smem_a;
-    // tile binning of the splat: per 16 x 8 x 32 tile the atoms whose cutoff box reaches it (CSR)
-    bool use_bins = false;     // false: the splat selects atoms per tile from the leaf boxes
-    int tiles[3] = {0, 0, 0};  // tiles along a, b, c
+    // tile bins of the splat: per 16 x 8 x 32 tile up to kBinCap atoms whose cutoff box reaches it
+    int tiles[3] = {0, 0, 0};   // tiles along a, b, c
     int n_tiles = 0;
-    long long bin_cap = 0;      // capacity of bin_list (a bound on the (atom, tile) pairs)
-    int* bin_count = nullptr;   // [n_tiles]
-    int* bin_off = nullptr;     // [n_tiles + 1]
-    int* bin_cursor = nullptr;  // [n_tiles]
-    int* bin_list = nullptr;    // [bin_cap]
+    int* bin_cursor = nullptr;  // [n_tiles] atoms that reached each tile (may exceed kBinCap)
+    int4* bin_list = nullptr;   // [n_tiles][kBinCap]: atom index, then st | cnt << 16 along a, b, c
     void* tc_dft = nullptr;     // HARTREE_FP32_TC_SPLIT: BF16 hi/lo 16-point DFT operands (forward, inverse)
 };
 
@@ -216,10 +213,9 @@ inline cudaError_t optin_smem(int* bytes) {
 // launchers (poisson.cu / atoms.cu); return cudaSuccess or the launch error
 cudaError_t launch_poisson(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s);
 cudaError_t launch_poisson_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
-// `prepared`: the per-atom boxes and factor arrays of these very positions are
-// already in the plan's workspace (an earlier launch on the same stream).
-cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s,
-                         bool prepared = false);
+// launch_splat prepares the per-atom boxes and factor arrays in the plan's workspace.
+// `prepared` (forces): they already hold these very positions (an earlier launch on the same stream).
+cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s);
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
                           double* phi, cudaStream_t s, bool prepared = false);
 void set_last_error(const char* msg);  // the message hartree_last_error() returns on this thread
