@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="diamond512", choices=["diamond512", "diamond256"],
-                    help="diamond256: the 4x4x4 cell on 256^3 (same density and sigma), for small profiler captures")
+    ap.add_argument("--workload", default="diamond512", choices=["diamond512", "diamond256", "ortho360"],
+                    help="diamond256: the 4x4x4 cell on 256^3 (same density and sigma), for small profiler captures; "
+                         "ortho360: the 37.9 x 40.4 x 42.1 Bohr cell on 360 x 384 x 400 (diamond density)")
     ap.add_argument("--skip-side", action="store_true", help="skip the e2e, adjoint and batched measurements")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16split"],
                     help="bf16split: b passes on the tensor cores (N2 = 256: the diamond256 workload)")
@@ -340,6 +341,10 @@ def main():
     if args.workload == "diamond512":
         S = synth.config3a()
         wl_text = "diamond 8x8x8 supercell, 4096 Gaussian charges (sigma 0.5 Bohr, cutoff 5 sigma), 512^3 grid"
+    elif args.workload == "ortho360":
+        S = synth.config3b()
+        wl_text = (f"orthorhombic 37.9 x 40.4 x 42.1 Bohr cell, {S.n_atoms} Gaussian charges at diamond density "
+                   "(sigma 0.5 Bohr, cutoff 5 sigma), 360 x 384 x 400 grid")
     else:
         S = synth.config5()
         wl_text = "diamond 4x4x4 supercell, 512 Gaussian charges (sigma 0.5 Bohr, cutoff 5 sigma), 256^3 grid"
@@ -454,8 +459,8 @@ def main():
                                               ", FP32 with tensor-core split b passes") +
                                    ": splat + Poisson + E_H + forces",
                        "grid": list(S.n), "atoms": S.n_atoms, "yardstick_bytes_per_step": ybytes,
-                       "l2": "inputs larger than L2 (each grid array 0.5 GB)" if S.n[0] == 512 else
-                             "working set larger than L2 (three 64 MB grid arrays); profiling case",
+                       "l2": f"inputs larger than L2 (each grid array {4 * ntot / 1e9:.2f} GB)" if 4 * ntot > 129e6
+                             else "working set larger than L2 (three 64 MB grid arrays); profiling case",
                        "parallelism": f"replicas x{world}", "variants": variants},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "solve_ms": solve_ms, "solve_gbs": ybytes / (solve_ms * 1e-3) / 1e9,

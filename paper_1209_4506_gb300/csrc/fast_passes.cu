@@ -130,10 +130,12 @@ template <typename T, int N, int R, int NS, int BPT, int JSTEP, int TWS, bool IN
 __device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, int j0, const Tw& TW,
                                        const Post& post, const Hook& hook = Hook{}) {
     constexpr int NB = N / R;
+    constexpr bool GUARD = NB % JSTEP != 0;  // mixed radices: the last round of butterflies is partial
     cpx<T> v[BPT][R];
 #pragma unroll
     for (int t = 0; t < BPT; ++t) {
         const int j = j0 + t * JSTEP;
+        if (GUARD && j >= NB) continue;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[t][r] = src.ld_(col, j + r * NB);
     }
@@ -147,6 +149,7 @@ __device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, 
 #pragma unroll
     for (int t = 0; t < BPT; ++t) {
         const int j = j0 + t * JSTEP;
+        if (GUARD && j >= NB) continue;
         const int k = j % NS;
         if constexpr (NS > 1) {
 #pragma unroll
@@ -169,14 +172,13 @@ template <typename T, int R0, int R1, int R2, int JSTEP, int TWS, bool INV, bool
 __device__ __forceinline__ void ftransform(const Src& src, const Sm& sm, const Dst& dst, int col, int j0,
                                            const Tw& TW, const Post& post, const Hook& hook = Hook{}) {
     constexpr int N = R0 * R1 * R2;
-    constexpr int B0 = (N / R0) / JSTEP, B1 = (N / R1) / JSTEP, B2 = (N / R2) / JSTEP;
-    static_assert(B0 * JSTEP * R0 == N && B1 * JSTEP * R1 == N, "butterflies must divide evenly");
+    constexpr int B0 = (N / R0 + JSTEP - 1) / JSTEP, B1 = (N / R1 + JSTEP - 1) / JSTEP,
+                  B2 = (N / R2 + JSTEP - 1) / JSTEP;
     if constexpr (R2 == 1) {
         fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{}, hook);
         __syncthreads();
         fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, dst, col, j0, TW, post);
     } else {
-        static_assert(B2 * JSTEP * R2 == N, "butterflies must divide evenly");
         fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{}, hook);
         __syncthreads();
         fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, sm, col, j0, TW, NoPost{});
@@ -194,10 +196,12 @@ __device__ __forceinline__ void ftransform(const Src& src, const Sm& sm, const D
 template <typename T, int N, int R, int BPT, int JSTEP, class Sm, class Tw, class Green>
 __device__ __forceinline__ void fstage_green_pivot(const Sm& sm, int col, int j0, const Tw& TW, const Green& green) {
     constexpr int NS = N / R;
+    constexpr bool GUARD = NS % JSTEP != 0;
     cpx<T> v[BPT][R];
 #pragma unroll
     for (int t = 0; t < BPT; ++t) {
         const int j = j0 + t * JSTEP;
+        if (GUARD && j >= NS) continue;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[t][r] = sm.ld_(col, j + r * NS);
     }
@@ -205,6 +209,7 @@ __device__ __forceinline__ void fstage_green_pivot(const Sm& sm, int col, int j0
 #pragma unroll
     for (int t = 0; t < BPT; ++t) {
         const int j = j0 + t * JSTEP;
+        if (GUARD && j >= NS) continue;
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[t][r] = twmul<true>(v[t][r], TW[j * r], false);
@@ -225,8 +230,8 @@ template <typename T, int R0, int R1, int R2, int JSTEP, bool FIRST_SYNC, class 
 __device__ __forceinline__ void ftransform_green(const Src& src, const Sm& sm, const Dst& dst, int col, int j0,
                                                  const Tw& TW, const Green& green) {
     constexpr int N = R0 * R1 * R2;
-    constexpr int B0 = (N / R0) / JSTEP, B1 = (N / R1) / JSTEP, B2 = (N / R2) / JSTEP;
-    static_assert(B0 * JSTEP * R0 == N && B1 * JSTEP * R1 == N, "butterflies must divide evenly");
+    constexpr int B0 = (N / R0 + JSTEP - 1) / JSTEP, B1 = (N / R1 + JSTEP - 1) / JSTEP,
+                  B2 = (N / R2 + JSTEP - 1) / JSTEP;
     fstage<T, N, R0, 1, B0, JSTEP, 1, false, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{});
     __syncthreads();
     if constexpr (R2 == 1) {
@@ -234,7 +239,6 @@ __device__ __forceinline__ void ftransform_green(const Src& src, const Sm& sm, c
         __syncthreads();
         fstage<T, N, R0, R1, B0, JSTEP, 1, true, true>(sm, dst, col, j0, TW, NoPost{});
     } else {
-        static_assert(B2 * JSTEP * R2 == N, "butterflies must divide evenly");
         fstage<T, N, R1, R0, B1, JSTEP, 1, false, true>(sm, sm, col, j0, TW, NoPost{});
         __syncthreads();
         fstage_green_pivot<T, N, R2, B2, JSTEP>(sm, col, j0, TW, green);
@@ -255,7 +259,8 @@ constexpr int min_ctas() {
 }
 
 template <typename T, int COLS, int NT, int R0, int R1, int R2, int MODE>
-__global__ void __launch_bounds__(NT, min_ctas<NT>()) k_col_fast(FastArgs<T> a) {
+__global__ void __launch_bounds__(NT, MODE == 2 && min_ctas<NT>() > 2 ? min_ctas<NT>() - 1 : min_ctas<NT>())
+    k_col_fast(FastArgs<T> a) {
     constexpr int N = R0 * R1 * R2;
     constexpr int JSTEP = NT / COLS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -300,6 +305,14 @@ __global__ void __launch_bounds__(NT, min_ctas<NT>()) k_col_fast(FastArgs<T> a) 
     }
 }
 
+// Rows of one tensor-map box along a column of n points: the largest divisor of n
+// within the 256-element box limit.
+__host__ __device__ constexpr int box_rows(int n) {
+    for (int r = n < 256 ? n : 256; r > 1; --r)
+        if (n % r == 0) return r;
+    return 1;
+}
+
 // ------------------------------------------------------------------ TMA-streamed b and a passes (FP32)
 // Persistent CTAs walk the tiles blockIdx.x, blockIdx.x + gridDim.x, ... through
 // a ring of NBUF shared-memory tile buffers.  Thread 0 keeps NBUF - 1 tile
@@ -315,7 +328,7 @@ __global__ void __launch_bounds__(NT, 1)
     k_col_tma(FastArgs<float> a, const __grid_constant__ CUtensorMap tmap, int ntiles, int chunks, int* err) {
     constexpr int N = R0 * R1 * R2;
     constexpr int JSTEP = NT / COLS;
-    constexpr int BOXR = N < 256 ? N : 256;  // rows per bulk copy (box dimension limit 256)
+    constexpr int BOXR = box_rows(N);  // rows per bulk copy (box dimension limit 256)
     constexpr int NBOX = N / BOXR;
     constexpr uint32_t TILE_BYTES = (uint32_t)N * COLS * 8;
     // All shared memory is dynamic (a static array would shift the dynamic base), and the tile
@@ -498,7 +511,7 @@ __global__ void __launch_bounds__(NT, 2)
     constexpr int TPL = NT / LINES;
     constexpr int LDP = M + M / 16 + 1;
     constexpr int SLOT = LINES * M;  // complex elements per ring slot
-    constexpr int B0 = (N / R0) / TPL, B1 = (N / R1) / TPL, B2 = (N / R2) / TPL;
+    constexpr int B0 = (N / R0 + TPL - 1) / TPL, B1 = (N / R1 + TPL - 1) / TPL, B2 = (N / R2 + TPL - 1) / TPL;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<float>* ring = reinterpret_cast<cpx<float>*>(smem_raw);
     cpx<float>* S = ring + NBUF * SLOT;
@@ -573,7 +586,7 @@ __global__ void __launch_bounds__(NT, 2) k_c2r_stream(float* __restrict__ vout, 
     constexpr int N = M;
     constexpr int TPL = NT / LINES;
     constexpr int LDP = M + M / 16 + 1;
-    constexpr int B0 = (N / R0) / TPL, B1 = (N / R1) / TPL, B2 = (N / R2) / TPL;
+    constexpr int B0 = (N / R0 + TPL - 1) / TPL, B1 = (N / R1 + TPL - 1) / TPL, B2 = (N / R2 + TPL - 1) / TPL;
     const int slot = LINES * a.ldc;  // complex elements per ring slot: LINES padded rows
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<float>* ring = reinterpret_cast<cpx<float>*>(smem_raw);
@@ -711,6 +724,7 @@ bool with_line_stream_cfg(int m, F&& f) {
         case 128: f(LineStreamCfg<32, 256, 16, 8, 1, 2>{}); return true;
         case 256: f(LineStreamCfg<16, 256, 16, 16, 1, 2>{}); return true;
         case 512: f(LineStreamCfg<8, 256, 8, 8, 8, 2>{}); return true;
+        case 200: f(LineStreamCfg<16, 256, 8, 5, 5, 2>{}); return true;
         default: return false;
     }
 }
@@ -751,6 +765,8 @@ bool with_col_tma_cfg(int n, int variant, F&& f) {
             else if (variant == 2) f(ColTmaCfg<256, 16, 32, 1, 3>{});
             else f(ColTmaCfg<512, 8, 8, 8, 3>{});
             return true;
+        case 360: f(ColTmaCfg<512, 8, 5, 9, 3>{}); return true;
+        case 384: f(ColTmaCfg<512, 16, 8, 3, 3>{}); return true;
         default: return false;
     }
 }
@@ -776,11 +792,13 @@ bool with_col_cfg(int n, int variant, F&& f) {
             else f(ColCfg<T, d ? 8 : 16, d ? 256 : 512, 8, 8, 8>{});
             return true;
         case 1024: f(ColCfg<T, 8, 512, 16, 8, 8>{}); return true;
+        case 360: f(ColCfg<T, d ? 8 : 16, 256, 8, 5, 9>{}); return true;
+        case 384: f(ColCfg<T, d ? 8 : 16, d ? 256 : 512, 16, 8, 3>{}); return true;
         default: return false;
     }
 }
 int col_variants(int n) { return (n == 256 || n == 512) ? 2 : 1; }
-int col_tma_variants(int n) { return n == 512 ? 3 : (n == 256 ? 2 : 0); }
+int col_tma_variants(int n) { return n == 512 ? 3 : (n == 256 ? 2 : (n == 360 || n == 384 ? 1 : 0)); }
 
 // Variants col_variants(n) .. of the b / a passes: the TMA-streamed kernels (FP32, plan has the tensor maps).
 bool col_tma_available(const Plan& p, int axis) {
@@ -808,6 +826,7 @@ bool with_line_cfg(int m, int variant, F&& f) {
             else f(LineCfg<T, 4, 256, 8, 8, 8>{});
             return true;
         case 1024: f(LineCfg<T, 4, 256, 16, 8, 8>{}); return true;
+        case 200: f(LineCfg<T, 16, 256, 8, 5, 5>{}); return true;
         default: return false;
     }
 }
@@ -993,8 +1012,8 @@ void prepare_tma(Plan& p) {
     if (p.prec == HARTREE_FP64) return;
     const uint64_t dims[3] = {(uint64_t)2 * p.ldc, (uint64_t)p.n[1], (uint64_t)p.n[0]};
     const uint64_t strides[2] = {(uint64_t)2 * p.ldc * 4, (uint64_t)p.n[1] * 2 * p.ldc * 4};
-    const uint32_t box_b[3] = {32, (uint32_t)(p.n[1] < 256 ? p.n[1] : 256), 1};
-    const uint32_t box_a[3] = {32, 1, (uint32_t)(p.n[0] < 256 ? p.n[0] : 256)};
+    const uint32_t box_b[3] = {32, (uint32_t)box_rows(p.n[1]), 1};
+    const uint32_t box_a[3] = {32, 1, (uint32_t)box_rows(p.n[0])};
     const bool ok_b = encode_tensor_map_3d(&p.tmap_b, p.W, dims, strides, box_b);
     const bool ok_a = encode_tensor_map_3d(&p.tmap_a, p.W, dims, strides, box_a);
     p.tma_ok = ok_a && ok_b && p.d_err != nullptr && p.sm_count > 0;

@@ -151,6 +151,37 @@ __host__ __device__ __forceinline__ void dft8(cpx<T>* v) {
     v[7] = e[3] - o3;
 }
 
+// Radix 9 as 3 x 3: with n = 3 n1 + n2 and k = k1 + 3 k2, three 3-point DFTs over
+// n1, the twiddles w9^(n2 k1), then three 3-point DFTs over n2.
+template <typename T, bool INV, bool COMP = true>
+__host__ __device__ __forceinline__ void dft9(cpx<T>* v) {
+    const double c1 = 0.766044443118978035, s1 = 0.642787609686539326;   // cos, sin(2 pi / 9)
+    const double c2 = 0.173648177666930349, s2 = 0.984807753012208059;   // cos, sin(4 pi / 9)
+    const double c4 = -0.939692620785908384, s4 = 0.342020143325668733;  // cos, sin(8 pi / 9)
+    const double sg = INV ? 1.0 : -1.0;
+    cpx<T> y[3][3];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2) {
+        cpx<T> t[3] = {v[n2], v[n2 + 3], v[n2 + 6]};
+        dft3<T, INV, COMP>(t);
+        y[n2][0] = t[0];
+        y[n2][1] = t[1];
+        y[n2][2] = t[2];
+    }
+    y[1][1] = kcmul<T, COMP>(y[1][1], c1, sg * s1);
+    y[1][2] = kcmul<T, COMP>(y[1][2], c2, sg * s2);
+    y[2][1] = kcmul<T, COMP>(y[2][1], c2, sg * s2);
+    y[2][2] = kcmul<T, COMP>(y[2][2], c4, sg * s4);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        cpx<T> t[3] = {y[0][k1], y[1][k1], y[2][k1]};
+        dft3<T, INV, COMP>(t);
+        v[k1] = t[0];
+        v[k1 + 3] = t[1];
+        v[k1 + 6] = t[2];
+    }
+}
+
 // Radix 16 and 32 from two halves of half the size and the twiddles
 // exp(-+ 2 pi i k / R) = cos(2 pi k / R) -+ i sin(2 pi k / R).
 template <typename T, int R, bool INV, bool COMP>
@@ -229,6 +260,7 @@ __host__ __device__ __forceinline__ void dft(cpx<T>* v) {
     if constexpr (R == 4) dft4<T, INV, COMP>(v);
     if constexpr (R == 5) dft5<T, INV, COMP>(v);
     if constexpr (R == 8) dft8<T, INV, COMP>(v);
+    if constexpr (R == 9) dft9<T, INV, COMP>(v);
     if constexpr (R == 16) dft16<T, INV, COMP>(v);
     if constexpr (R == 32) dft32<T, INV, COMP>(v);
 }
