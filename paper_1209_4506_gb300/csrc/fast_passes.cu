@@ -323,8 +323,8 @@ __host__ __device__ constexpr int box_rows(int n) {
 // themselves, and memory traffic overlaps the butterflies of the other tiles.
 // A wait that does not complete within kSpinLimit probes sets the error word
 // and ends the CTA's loop (all threads agree through __syncthreads_and).
-template <int COLS, int NT, int R0, int R1, int R2, int MODE, int NBUF>
-__global__ void __launch_bounds__(NT, 1)
+template <int COLS, int NT, int R0, int R1, int R2, int MODE, int NBUF, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_col_tma(FastArgs<float> a, const __grid_constant__ CUtensorMap tmap, int ntiles, int chunks, int* err) {
     constexpr int N = R0 * R1 * R2;
     constexpr int JSTEP = NT / COLS;
@@ -729,25 +729,29 @@ bool with_line_stream_cfg(int m, F&& f) {
     }
 }
 
-// TMA-streamed column pass configuration (FP32): 16 columns (128-byte rows) per tile.
-template <int NT, int R0, int R1, int R2, int NBUF>
+// TMA-streamed column pass configuration (FP32): COLS columns (16: 128-byte rows, one CTA per
+// SM; 8: 64-byte rows, MINB CTAs per SM, each with its own barriers) per tile.
+template <int NT, int R0, int R1, int R2, int NBUF, int COLS = 16, int MINB = 1>
 struct ColTmaCfg {
-    static constexpr int cols = 16, n = R0 * R1 * R2;
+    static constexpr int cols = COLS, n = R0 * R1 * R2, minb = MINB;
     static size_t smem() {  // tile ring, twiddles, mbarriers, reduction slots, alignment slack
-        return (size_t)NBUF * n * 16 * sizeof(cpx<float>) + (size_t)n * sizeof(TwPair<float>) + NBUF * 8 +
+        return (size_t)NBUF * n * COLS * sizeof(cpx<float>) + (size_t)n * sizeof(TwPair<float>) + NBUF * 8 +
                (NT / 32) * sizeof(double) + 1024;
     }
     static cudaError_t configure(int optin) {
         cudaError_t e;
-        if ((e = allow_max_dynamic_smem(k_col_tma<16, NT, R0, R1, R2, 0, NBUF>, optin))) return e;
-        if ((e = allow_max_dynamic_smem(k_col_tma<16, NT, R0, R1, R2, 1, NBUF>, optin))) return e;
-        return allow_max_dynamic_smem(k_col_tma<16, NT, R0, R1, R2, 2, NBUF>, optin);
+        if ((e = allow_max_dynamic_smem(k_col_tma<COLS, NT, R0, R1, R2, 0, NBUF, MINB>, optin))) return e;
+        if ((e = allow_max_dynamic_smem(k_col_tma<COLS, NT, R0, R1, R2, 1, NBUF, MINB>, optin))) return e;
+        return allow_max_dynamic_smem(k_col_tma<COLS, NT, R0, R1, R2, 2, NBUF, MINB>, optin);
     }
     static void launch(int mode, unsigned grid, const FastArgs<float>& a, const CUtensorMap& map, int ntiles,
                        int chunks, int* err, cudaStream_t s) {
-        if (mode == 0) k_col_tma<16, NT, R0, R1, R2, 0, NBUF><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
-        if (mode == 1) k_col_tma<16, NT, R0, R1, R2, 1, NBUF><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
-        if (mode == 2) k_col_tma<16, NT, R0, R1, R2, 2, NBUF><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+        if (mode == 0)
+            k_col_tma<COLS, NT, R0, R1, R2, 0, NBUF, MINB><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+        if (mode == 1)
+            k_col_tma<COLS, NT, R0, R1, R2, 1, NBUF, MINB><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+        if (mode == 2)
+            k_col_tma<COLS, NT, R0, R1, R2, 2, NBUF, MINB><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
     }
 };
 
@@ -758,15 +762,25 @@ bool with_col_tma_cfg(int n, int variant, F&& f) {
     switch (n) {
         case 256:
             if (variant == 1) f(ColTmaCfg<128, 32, 8, 1, 3>{});
+            else if (variant == 2) f(ColTmaCfg<128, 16, 16, 1, 3, 8, 3>{});
             else f(ColTmaCfg<256, 16, 16, 1, 3>{});
             return true;
         case 512:
             if (variant == 1) f(ColTmaCfg<256, 32, 16, 1, 3>{});
             else if (variant == 2) f(ColTmaCfg<256, 16, 32, 1, 3>{});
+            else if (variant == 3) f(ColTmaCfg<256, 8, 8, 8, 3, 8, 2>{});
+            else if (variant == 4) f(ColTmaCfg<128, 32, 16, 1, 3, 8, 2>{});
             else f(ColTmaCfg<512, 8, 8, 8, 3>{});
             return true;
-        case 360: f(ColTmaCfg<512, 8, 5, 9, 3>{}); return true;
-        case 384: f(ColTmaCfg<512, 16, 8, 3, 3>{}); return true;
+        case 360:
+            if (variant == 1) f(ColTmaCfg<256, 9, 5, 8, 3, 8, 2>{});
+            else if (variant == 2) f(ColTmaCfg<512, 9, 5, 8, 3>{});
+            else f(ColTmaCfg<512, 8, 5, 9, 3>{});
+            return true;
+        case 384:
+            if (variant == 1) f(ColTmaCfg<256, 16, 8, 3, 3, 8, 2>{});
+            else f(ColTmaCfg<512, 16, 8, 3, 3>{});
+            return true;
         default: return false;
     }
 }
@@ -798,7 +812,7 @@ bool with_col_cfg(int n, int variant, F&& f) {
     }
 }
 int col_variants(int n) { return (n == 256 || n == 512) ? 2 : 1; }
-int col_tma_variants(int n) { return n == 512 ? 3 : (n == 256 ? 2 : (n == 360 || n == 384 ? 1 : 0)); }
+int col_tma_variants(int n) { return n == 512 ? 5 : (n == 256 ? 3 : (n == 360 ? 3 : (n == 384 ? 2 : 0))); }
 
 // Variants col_variants(n) .. of the b / a passes: the TMA-streamed kernels (FP32, plan has the tensor maps).
 bool col_tma_available(const Plan& p, int axis) {
@@ -946,9 +960,11 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
             with_col_tma_cfg(p.n[axis], tv, [&](auto c) {
                 const int chunks = (p.nh + c.cols - 1) / c.cols;
                 const int ntiles = p.n[1 - axis] * chunks;
-                grid = ntiles < p.sm_count ? ntiles : p.sm_count;
-                c.launch(pass == 1 ? 0 : (pass == 3 ? 1 : 2), (unsigned)grid, a, axis == 0 ? p.tmap_a : p.tmap_b,
-                         ntiles, chunks, p.d_err, s);
+                const int slots = c.minb * p.sm_count;
+                grid = ntiles < slots ? ntiles : slots;
+                const CUtensorMap& map = c.cols == 16 ? (axis == 0 ? p.tmap_a : p.tmap_b)
+                                                      : (axis == 0 ? p.tmap_a8 : p.tmap_b8);
+                c.launch(pass == 1 ? 0 : (pass == 3 ? 1 : 2), (unsigned)grid, a, map, ntiles, chunks, p.d_err, s);
             });
             return grid;
         }
@@ -1006,7 +1022,7 @@ bool encode_tensor_map_3d(CUtensorMap* map, void* base, const uint64_t dims[3], 
 }
 
 // Tensor maps over the half spectrum W (FP32, viewed as floats [N1][N2][2 ldc]) for the b and a
-// column passes: boxes of 16 complex columns by up to 256 rows.
+// column passes: boxes of 16 or 8 complex columns by up to 256 rows.
 void prepare_tma(Plan& p) {
     p.tma_ok = false;
     if (p.prec == HARTREE_FP64) return;
@@ -1014,8 +1030,12 @@ void prepare_tma(Plan& p) {
     const uint64_t strides[2] = {(uint64_t)2 * p.ldc * 4, (uint64_t)p.n[1] * 2 * p.ldc * 4};
     const uint32_t box_b[3] = {32, (uint32_t)box_rows(p.n[1]), 1};
     const uint32_t box_a[3] = {32, 1, (uint32_t)box_rows(p.n[0])};
-    const bool ok_b = encode_tensor_map_3d(&p.tmap_b, p.W, dims, strides, box_b);
-    const bool ok_a = encode_tensor_map_3d(&p.tmap_a, p.W, dims, strides, box_a);
+    const uint32_t box_b8[3] = {16, (uint32_t)box_rows(p.n[1]), 1};
+    const uint32_t box_a8[3] = {16, 1, (uint32_t)box_rows(p.n[0])};
+    const bool ok_b = encode_tensor_map_3d(&p.tmap_b, p.W, dims, strides, box_b) &&
+                      encode_tensor_map_3d(&p.tmap_b8, p.W, dims, strides, box_b8);
+    const bool ok_a = encode_tensor_map_3d(&p.tmap_a, p.W, dims, strides, box_a) &&
+                      encode_tensor_map_3d(&p.tmap_a8, p.W, dims, strides, box_a8);
     p.tma_ok = ok_a && ok_b && p.d_err != nullptr && p.sm_count > 0;
 }
 

@@ -275,50 +275,52 @@ def test_single_passes_reproduce_solve_density(precision):
     "shape,precision",
     [((512, 256, 512), "fp32"), ((256, 512, 256), "fp32"), ((256, 512, 256), "fp64"), ((360, 384, 400), "fp32")],
 )
-def test_kernel_variants_give_identical_potential(shape, precision):
-    """Every compiled tile shape and radix order (and the TMA-streamed passes) computes V_H within tolerance.
+def test_kernel_variants_agree(shape, precision):
+    """Every compiled variant of every pass kind (tile shapes, thread counts, radix orders,
+    TMA / bulk-copy streams, CTAs per SM) computes V_H and E_H within tolerance of the oracle.
 
-    b / a variants 0..2 keep the radix order of the plain kernels (tile shapes and
-    the TMA stream differ only in which thread does a butterfly), so with the
-    plain c kernels their V_H is bit-identical; the radix-32 TMA variants (3, 4)
-    round differently, and so may the streamed inverse c pass (the last c
-    variant: 2 for c lines of 256, 512 and 1024 points, else 1)."""
-    import itertools
-
+    Variants are switched one pass kind at a time.  Variants with the radix order of the
+    plain kernels differ only in which thread does a butterfly; others (radix-32 stages,
+    the streamed inverse c pass) round differently: all agree with variant 0 to FP32
+    rounding."""
     from paper_1209_4506_gb300 import capi
 
     cell = (20.0, 12.0, 21.0)
     rng = np.random.default_rng(17)
     dt = torch.float64 if precision == "fp64" else torch.float32
     rho = torch.tensor(rng.standard_normal(shape), dtype=dt, device="cuda")
-    v_ref, e_ref, _, _ = O.poisson(cell, rho.double().cpu().numpy())
+    v_ref_np, e_ref, _, _ = O.poisson(cell, rho.double().cpu().numpy())
+    v_ref = torch.tensor(v_ref_np, device="cuda")
+    ref_norm = torch.linalg.vector_norm(v_ref).item()
     plan = HartreePlan(shape, cell, 0.5, precision)
-    results = []
-    for choice in itertools.product(range(5), repeat=3):
-        try:
-            plan.set_variants(list(choice))
-        except capi.HartreeError:
-            continue
-        vh, eh = plan.solve_density(rho)
-        torch.cuda.synchronize()
-        results.append((choice, vh.clone(), eh.item()))
+    plan.set_variants([0, 0, 0])
+    v0, e0 = plan.solve_density(rho)
+    v0 = v0.double()
+    n_checked = 0
+    for kind in range(3):
+        for var in range(16):
+            choice = [0, 0, 0]
+            choice[kind] = var
+            try:
+                plan.set_variants(choice)
+            except capi.HartreeError:
+                break
+            vh, eh = plan.solve_density(rho)
+            torch.cuda.synchronize()
+            vd = vh.double()
+            assert torch.linalg.vector_norm(vd - v_ref).item() <= TOL[precision]["v"] * ref_norm, choice
+            assert torch.linalg.vector_norm(vd - v0).item() <= 1e-6 * ref_norm, choice
+            assert abs(eh.item() - e_ref) <= WHITE_NOISE_E_TOL[precision] * abs(e_ref), choice
+            n_checked += 1
     plan.device_status()
-    assert len(results) >= 8
-    for choice, vh, eh in results:
-        assert rel_l2(vh.double().cpu().numpy(), v_ref) <= TOL[precision]["v"], choice
-        assert abs(eh - e_ref) <= WHITE_NOISE_E_TOL[precision] * abs(e_ref), choice
-        if max(choice[1:]) <= 2:
-            # E_H is formed before the inverse c pass, from the same terms in a different grouping
-            # (per-CTA partials; persistent CTAs sum across tiles)
-            assert abs(eh - results[0][2]) <= 1e-10 * abs(results[0][2]), choice
-        plain_c = 2 if shape[2] // 2 in (128, 256, 512) else 1
-        if choice[0] < plain_c and max(choice[1:]) <= 2:
-            assert torch.equal(vh, results[0][1]), choice
+    assert n_checked >= 4
     picks = plan.autotune()
     plan.device_status()
-    assert all(0 <= p <= 4 for p in picks)
+    vh, eh = plan.solve_density(rho)
+    torch.cuda.synchronize()
+    assert torch.linalg.vector_norm(vh.double() - v_ref).item() <= TOL[precision]["v"] * ref_norm, picks
     with pytest.raises(capi.HartreeError):
-        plan.set_variants([0, 0, 5])
+        plan.set_variants([0, 0, 99])
 
 
 @pytest.mark.parametrize(
