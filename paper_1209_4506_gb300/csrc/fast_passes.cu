@@ -37,6 +37,10 @@ __device__ __forceinline__ cpx<T> twmul(cpx<T> a, const TwPair<T>& w, bool inv) 
     }
 }
 
+// 1 / x rounded to nearest: the reciprocal instruction sequence, not the general division
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
+
 template <int R0, int R1, int R2>
 struct RP {
     static constexpr int N = R0 * R1 * R2;
@@ -290,7 +294,7 @@ __global__ void __launch_bounds__(NT, MODE == 2 && min_ctas<NT>() > 2 ? min_ctas
         auto green = [&](int c, int k1, cpx<T>& v) {
             const cpx<T> ga = a.gsqa[k1];
             const T G2 = ((ga.re + gb.re) + gc.re) + ((ga.im + gb.im) + gc.im);
-            const T inv = (G2 > T(0)) ? T(1) / G2 : T(0);
+            const T inv = (G2 > T(0)) ? recip_rn(G2) : T(0);
             if (c < nc) {
                 const T term = mult * (v.re * v.re + v.im * v.im) * inv - comp;
                 const T t = sum + term;
@@ -398,7 +402,7 @@ __global__ void __launch_bounds__(NT, MINB)
             auto green = [&](int c, int k1, cpx<float>& v) {
                 const cpx<float> ga = a.gsqa[k1];
                 const float G2 = ((ga.re + gb.re) + gc.re) + ((ga.im + gb.im) + gc.im);
-                const float inv = (G2 > 0.f) ? 1.f / G2 : 0.f;
+                const float inv = (G2 > 0.f) ? __frcp_rn(G2) : 0.f;  // = 1 / G2, correctly rounded
                 if (c < nc) {
                     const float term = mult * (v.re * v.re + v.im * v.im) * inv - comp;
                     const float tt = sum + term;
@@ -446,17 +450,21 @@ __global__ void __launch_bounds__(NT, min_ctas<NT>()) k_r2c_fast(const T* __rest
     // M-point transform of z (twiddles exp(-2 pi i e / M) = table entry 2e)
     ftransform<T, R0, R1, R2, TPL, 2, false, false>(src, sm, sm, 0, j0, TW, NoPost{});
     __syncthreads();
-    // X[k] = E[k] + w^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M
+    // X[k] = E[k] + w^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M;
+    // the pair k, M - k shares its loads: E[M-k] = conj E[k], O[M-k] = conj O[k], w^(M-k) = -conj w^k,
+    // so X[M-k] = conj(E[k] - w^k O[k])
     if (act) {
         cpx<T>* out = a.W + gline * a.ldc;
         const T half = T(0.5);
-        for (int k = j0; k <= M; k += TPL) {
-            const cpx<T> z1 = sm.ld_(0, k == M ? 0 : k);
+        for (int k = j0; k <= M / 2; k += TPL) {
+            const cpx<T> z1 = sm.ld_(0, k);
             const cpx<T> z2 = conjg(sm.ld_(0, k == 0 ? 0 : M - k));
             const cpx<T> E = scale(z1 + z2, half);
             const cpx<T> d = z1 - z2;
             const cpx<T> O = mk(d.im * half, -d.re * half);
-            out[k] = E + twmul(O, TW[k], false);
+            const cpx<T> t = twmul(O, TW[k], false);
+            out[k] = E + t;
+            out[M - k] = conjg(E - t);
         }
     }
 }
@@ -565,16 +573,18 @@ __global__ void __launch_bounds__(NT, 2)
             fstage<float, N, R2, R0 * R1, B2, TPL, 2, false, true>(sm, sm, 0, j0, TW, NoPost{});
         }
         __syncthreads();
-        // X[k] = E[k] + w^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M
+        // X[k] and X[M - k] from one pair of loads, as in k_r2c_fast
         if (act) {
             cpx<float>* out = a.W + gline * a.ldc;
-            for (int kk = j0; kk <= M; kk += TPL) {
-                const cpx<float> z1 = sm.ld_(0, kk == M ? 0 : kk);
+            for (int kk = j0; kk <= M / 2; kk += TPL) {
+                const cpx<float> z1 = sm.ld_(0, kk);
                 const cpx<float> z2 = conjg(sm.ld_(0, kk == 0 ? 0 : M - kk));
                 const cpx<float> E = scale(z1 + z2, 0.5f);
                 const cpx<float> d = z1 - z2;
                 const cpx<float> O = mk(d.im * 0.5f, -d.re * 0.5f);
-                out[kk] = E + twmul(O, TW[kk], false);
+                const cpx<float> t = twmul(O, TW[kk], false);
+                out[kk] = E + t;
+                out[M - kk] = conjg(E - t);
             }
         }
     }
