@@ -64,5 +64,6 @@ def test_full_size_step_matches_oracle(name):
     assert abs(eh_o - eh_spec) <= 1e-10 * abs(eh_o)
     assert np.max(np.abs(f_g - f_o)) <= 1e-5
     assert np.max(np.abs(phi_g - phi_o)) <= 1e-5
-    assert np.max(np.abs(f_g.sum(axis=0))) <= 1e-5  # Newton's third law
+    # Newton's third law: sum F = 0 up to the FP32 error of the 4 N_atoms terms (relative to sum |F|)
+    assert np.max(np.abs(f_g.sum(axis=0))) <= 1e-7 * np.abs(f_o).sum()
     plan.close()
