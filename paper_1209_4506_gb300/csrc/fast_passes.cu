@@ -398,20 +398,24 @@ __global__ void __launch_bounds__(NT, MINB)
             const cpx<float> gb = a.gsqb[line];
             const int k3 = c0 + col;
             const cpx<float> gc = a.gsqc[k3 < a.nh ? k3 : 0];
+            // |G|^2 = |G_a|^2 + (|G_b|^2 + |G_c|^2): the b + c part once per tile, high and low parts apart
+            const float gbc_h = gb.re + gc.re, gbc_l = gb.im + gc.im;
             const float mult = (k3 == 0 || k3 == a.M) ? 1.f : 2.f;
+            float tile_sum = 0.f;  // this thread's terms of this tile (its column, BPT R rows)
             auto green = [&](int c, int k1, cpx<float>& v) {
-                const cpx<float> ga = a.gsqa[k1];
-                const float G2 = ((ga.re + gb.re) + gc.re) + ((ga.im + gb.im) + gc.im);
+                const float2 ga = __ldg(reinterpret_cast<const float2*>(a.gsqa + k1));
+                const float G2 = (ga.x + gbc_h) + (ga.y + gbc_l);
                 const float inv = (G2 > 0.f) ? __frcp_rn(G2) : 0.f;  // = 1 / G2, correctly rounded
-                if (c < nc) {
-                    const float term = mult * (v.re * v.re + v.im * v.im) * inv - comp;
-                    const float tt = sum + term;
-                    comp = (tt - sum) - term;
-                    sum = tt;
-                }
+                tile_sum = fmaf(v.re * v.re + v.im * v.im, inv, tile_sum);
                 v = scale(v, inv * a.green_scale);
             };
             ftransform_green<float, R0, R1, R2, JSTEP, true>(sm, sm, sm, col, j0, TW, green);
+            if (col < nc) {  // compensated across tiles
+                const float term = mult * tile_sum - comp;
+                const float tt = sum + term;
+                comp = (tt - sum) - term;
+                sum = tt;
+            }
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -748,6 +752,22 @@ struct ColTmaCfg {
         return (size_t)NBUF * n * COLS * sizeof(cpx<float>) + (size_t)n * sizeof(TwPair<float>) + NBUF * 8 +
                (NT / 32) * sizeof(double) + 1024;
     }
+    // CTAs per SM the launch relies on: MINB, or fewer if they do not fit
+    static int resident(int mode) {
+        static int r[3] = {0, 0, 0};
+        if (r[mode] == 0) {
+            int b = 0;
+            cudaError_t e = mode == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 0, NBUF, MINB>, NT, smem())
+                            : mode == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 1, NBUF, MINB>, NT, smem())
+                                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 2, NBUF, MINB>, NT, smem());
+            if (e != cudaSuccess) cudaGetLastError();
+            r[mode] = e == cudaSuccess && b > 0 ? (b < MINB ? b : MINB) : 1;
+        }
+        return r[mode];
+    }
     static cudaError_t configure(int optin) {
         cudaError_t e;
         if ((e = allow_max_dynamic_smem(k_col_tma<COLS, NT, R0, R1, R2, 0, NBUF, MINB>, optin))) return e;
@@ -780,6 +800,7 @@ bool with_col_tma_cfg(int n, int variant, F&& f) {
             else if (variant == 2) f(ColTmaCfg<256, 16, 32, 1, 3>{});
             else if (variant == 3) f(ColTmaCfg<256, 8, 8, 8, 3, 8, 2>{});
             else if (variant == 4) f(ColTmaCfg<128, 32, 16, 1, 3, 8, 2>{});
+            else if (variant == 5) f(ColTmaCfg<256, 8, 8, 8, 2, 8, 3>{});
             else f(ColTmaCfg<512, 8, 8, 8, 3>{});
             return true;
         case 360:
@@ -822,7 +843,7 @@ bool with_col_cfg(int n, int variant, F&& f) {
     }
 }
 int col_variants(int n) { return (n == 256 || n == 512) ? 2 : 1; }
-int col_tma_variants(int n) { return n == 512 ? 5 : (n == 256 ? 3 : (n == 360 ? 3 : (n == 384 ? 2 : 0))); }
+int col_tma_variants(int n) { return n == 512 ? 6 : (n == 256 ? 3 : (n == 360 ? 3 : (n == 384 ? 2 : 0))); }
 
 // Variants col_variants(n) .. of the b / a passes: the TMA-streamed kernels (FP32, plan has the tensor maps).
 bool col_tma_available(const Plan& p, int axis) {
@@ -970,7 +991,8 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
             with_col_tma_cfg(p.n[axis], tv, [&](auto c) {
                 const int chunks = (p.nh + c.cols - 1) / c.cols;
                 const int ntiles = p.n[1 - axis] * chunks;
-                const int slots = c.minb * p.sm_count;
+                const int mode = pass == 1 ? 0 : (pass == 3 ? 1 : 2);
+                const int slots = c.resident(mode) * p.sm_count;
                 grid = ntiles < slots ? ntiles : slots;
                 const CUtensorMap& map = c.cols == 16 ? (axis == 0 ? p.tmap_a : p.tmap_b)
                                                       : (axis == 0 ? p.tmap_a8 : p.tmap_b8);
