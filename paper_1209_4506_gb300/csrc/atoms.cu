@@ -72,9 +72,12 @@ __device__ __forceinline__ AxisTiles axis_tiles(int lo, int cnt, int n, int T, i
 // further lookup.  Slots are taken with atomics, so a list is unordered (the
 // splat sorts it); a tile reached by more than kBinCap atoms keeps counting and
 // the splat then selects its atoms from the leaf boxes instead.
+constexpr int kSetupThreads = 512;  // one warp per atom of a leaf (16 atoms per leaf by default)
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_leaf_setup(AtomArgs<T> a, int tA, int tB, int tC, int* __restrict__ cursor,
-                                                   int4* __restrict__ list, bool bins) {
+__global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int tA, int tB, int tC,
+                                                             int* __restrict__ cursor, int4* __restrict__ list,
+                                                             bool bins) {
     __shared__ int bmin[3], bmax[3];
     const int l = blockIdx.x;
     const int i0 = l * a.apl, i1 = min(a.n, i0 + a.apl);
@@ -104,7 +107,9 @@ __global__ void __launch_bounds__(128) k_leaf_setup(AtomArgs<T> a, int tA, int t
         a.leaf[6 * l + d] = bmin[d];
         a.leaf[6 * l + 3 + d] = min(bmax[d] - bmin[d], ns[d]);
     }
-    for (int i = i0; i < i1; ++i) {
+    // one warp per atom appends it to its tiles' lists
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int i = i0 + (int)(threadIdx.x >> 5); i < i1; i += nwarps) {
         const AtomPrep<T> p = a.prep[i];
         const AxisTiles ra = axis_tiles(p.lo[0], p.cnt[0], a.n1, TA, tA);
         const AxisTiles rb = axis_tiles(p.lo[1], p.cnt[1], a.n2, TB, tB);
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(128) k_leaf_setup(AtomArgs<T> a, int tA, int t
         const int tot = ra.count * nbc;
         const int4 entry = make_int4(i, p.st[0] | (p.cnt[0] << 16), p.st[1] | (p.cnt[1] << 16),
                                      p.st[2] | (p.cnt[2] << 16));
-        for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+        for (int k = lane; k < tot; k += 32) {
             const int ka = k / nbc, r = k - ka * nbc, kb = r / rc.count, kc = r - kb * rc.count;
             const int tile = (ra.tile(ka) * tB + rb.tile(kb)) * tC + rc.tile(kc);
             const int slot = atomicAdd(cursor + tile, 1);
@@ -442,7 +447,8 @@ cudaError_t prep_atoms(const Plan& p, const AtomArgs<T>& a, bool bins, cudaStrea
     }
     if (a.n == 0) return cudaSuccess;
     p.launches += 1;
-    k_leaf_setup<T><<<a.nleaves, 128, 0, s>>>(a, p.tiles[0], p.tiles[1], p.tiles[2], p.bin_cursor, p.bin_list, bins);
+    k_leaf_setup<T><<<a.nleaves, kSetupThreads, 0, s>>>(a, p.tiles[0], p.tiles[1], p.tiles[2], p.bin_cursor,
+                                                         p.bin_list, bins);
     return cudaGetLastError();
 }
 
