@@ -43,9 +43,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="diamond512", choices=["diamond512", "diamond256", "ortho360"],
+    ap.add_argument("--workload", default="diamond512", choices=["diamond512", "diamond256", "ortho360", "paper420"],
                     help="diamond256: the 4x4x4 cell on 256^3 (same density and sigma), for small profiler captures; "
-                         "ortho360: the 37.9 x 40.4 x 42.1 Bohr cell on 360 x 384 x 400 (diamond density)")
+                         "ortho360: the 37.9 x 40.4 x 42.1 Bohr cell on 360 x 384 x 400 (diamond density); "
+                         "paper420: 16,384 diamond atoms on the 420 x 420 x 210 grid of the paper's benchmarks")
     ap.add_argument("--skip-side", action="store_true", help="skip the e2e, adjoint and batched measurements")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16split"],
                     help="bf16split: b passes on the tensor cores (N2 = 256: the diamond256 workload)")
@@ -341,6 +342,10 @@ def main():
     if args.workload == "diamond512":
         S = synth.config3a()
         wl_text = "diamond 8x8x8 supercell, 4096 Gaussian charges (sigma 0.5 Bohr, cutoff 5 sigma), 512^3 grid"
+    elif args.workload == "paper420":
+        S = synth.config_paper420()
+        wl_text = ("diamond 16x16x8 supercell, 16384 Gaussian charges (sigma 0.8 Bohr, cutoff 5 sigma), "
+                   "420 x 420 x 210 grid (h = 0.257 Bohr)")
     elif args.workload == "ortho360":
         S = synth.config3b()
         wl_text = (f"orthorhombic 37.9 x 40.4 x 42.1 Bohr cell, {S.n_atoms} Gaussian charges at diamond density "

@@ -64,7 +64,7 @@ typedef enum {
 typedef enum {
     HARTREE_OK = 0,
     HARTREE_ERR_INVALID = 1,          /* null pointer, bad count, sigma <= 0, NaN/Inf ... */
-    HARTREE_ERR_UNSUPPORTED_SIZE = 2, /* a grid size that is not 2/3/5-smooth, odd N3 ...  */
+    HARTREE_ERR_UNSUPPORTED_SIZE = 2, /* a grid size that is not 2/3/5/7-smooth, odd N3 ... */
     HARTREE_ERR_CUDA = 3,             /* a CUDA runtime call failed                        */
     HARTREE_ERR_OOM = 4,              /* device allocation failed in a *_create call       */
     HARTREE_ERR_TIMEOUT = 5,          /* a bounded device wait gave up (batched form)      */
@@ -72,7 +72,7 @@ typedef enum {
 } hartree_status;
 
 typedef struct {
-    int n[3];             /* grid points N1, N2, N3; 2/3/5-smooth, 2 <= N_d <= 4096, N3 even >= 4 */
+    int n[3];             /* grid points N1, N2, N3; 2/3/5/7-smooth, 2 <= N_d <= 4096, N3 even >= 4 */
     double cell[3];       /* L1, L2, L3 in Bohr, > 0                                        */
     double sigma;         /* Gaussian width s in Bohr, > 0                                  */
     double cutoff_sigmas; /* per-axis truncation radius in units of s; 0 = default

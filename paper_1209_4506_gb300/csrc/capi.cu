@@ -30,15 +30,15 @@ int cuda_fail(cudaError_t e, const char* where) {
     return fail(HARTREE_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-bool smooth235(int n) {
+bool smooth_size(int n) {  // 2/3/5/7-smooth
     if (n < 1) return false;
-    for (int p : {2, 3, 5})
+    for (int p : {2, 3, 5, 7})
         while (n % p == 0) n /= p;
     return n == 1;
 }
 
 // Radices for a line of length n: powers of two in balanced stages of at
-// most 16, then the factors 3 and 5 one stage each.
+// most 16, then the factors 3, 5 and 7 one stage each.
 bool make_radix_plan(int n, RadixPlan* rp) {
     rp->n = n;
     rp->nst = 0;
@@ -47,7 +47,7 @@ bool make_radix_plan(int n, RadixPlan* rp) {
         m /= 2;
         ++e2;
     }
-    int n3 = 0, n5 = 0;
+    int n3 = 0, n5 = 0, n7 = 0;
     while (m % 3 == 0) {
         m /= 3;
         ++n3;
@@ -55,6 +55,10 @@ bool make_radix_plan(int n, RadixPlan* rp) {
     while (m % 5 == 0) {
         m /= 5;
         ++n5;
+    }
+    while (m % 7 == 0) {
+        m /= 7;
+        ++n7;
     }
     if (m != 1) return false;
     if (e2 > 0) {
@@ -66,6 +70,7 @@ bool make_radix_plan(int n, RadixPlan* rp) {
     }
     for (int i = 0; i < n3; ++i) rp->r[rp->nst++] = 3;
     for (int i = 0; i < n5; ++i) rp->r[rp->nst++] = 5;
+    for (int i = 0; i < n7; ++i) rp->r[rp->nst++] = 7;
     if (rp->nst == 0) rp->r[rp->nst++] = 2;  // n == 1 never reaches here (n >= 2)
     return rp->nst <= kMaxStages;
 }
@@ -171,8 +176,8 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
     if (d.precision != HARTREE_FP64 && d.precision != HARTREE_FP32 && d.precision != HARTREE_FP32_TC_SPLIT)
         return fail(HARTREE_ERR_INVALID, "plan_create: unknown precision %d", d.precision);
     for (int i = 0; i < 3; ++i) {
-        if (d.n[i] < 2 || d.n[i] > kMaxAxis || !smooth235(d.n[i]))
-            return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: N%d = %d is not a 2/3/5-smooth size in [2, %d]",
+        if (d.n[i] < 2 || d.n[i] > kMaxAxis || !smooth_size(d.n[i]))
+            return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: N%d = %d is not a 2/3/5/7-smooth size in [2, %d]",
                         i + 1, d.n[i], kMaxAxis);
         if (!(d.cell[i] > 0.0) || !std::isfinite(d.cell[i]))
             return fail(HARTREE_ERR_INVALID, "plan_create: cell[%d] must be positive and finite", i);

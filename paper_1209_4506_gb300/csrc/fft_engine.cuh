@@ -151,6 +151,38 @@ __host__ __device__ __forceinline__ void dft8(cpx<T>* v) {
     v[7] = e[3] - o3;
 }
 
+// Radix 7 from the symmetric pairs a_k = x_k + x_(7-k), b_k = x_k - x_(7-k):
+// X[m] = p_m -+ i q_m and X[7-m] = p_m +- i q_m with p_m = x_0 + sum_k a_k cos(2 pi k m / 7)
+// and q_m = sum_k b_k sin(2 pi k m / 7).
+template <typename T, bool INV, bool COMP = true>
+__host__ __device__ __forceinline__ void dft7(cpx<T>* v) {
+    const double C[4] = {1.0, 0.623489801858733530525, -0.222520933956314404289, -0.900968867902419126236};
+    const double S[4] = {0.0, 0.781831482468029808708, 0.974927912181823607018, 0.433883739117558120475};
+    cpx<T> a[4], b[4];
+#pragma unroll
+    for (int k = 1; k <= 3; ++k) {
+        a[k] = v[k] + v[7 - k];
+        b[k] = v[k] - v[7 - k];
+    }
+    const cpx<T> x0 = v[0];
+    v[0] = ((x0 + a[1]) + a[2]) + a[3];
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+        cpx<T> pm = x0, qm = mk(T(0), T(0));
+#pragma unroll
+        for (int k = 1; k <= 3; ++k) {
+            const int j = (k * m) % 7;
+            const double cj = j <= 3 ? C[j] : C[7 - j];
+            const double sj = j <= 3 ? S[j] : -S[7 - j];
+            pm = mk(pm.re + kmul<T, COMP>(a[k].re, cj), pm.im + kmul<T, COMP>(a[k].im, cj));
+            qm = mk(qm.re + kmul<T, COMP>(b[k].re, sj), qm.im + kmul<T, COMP>(b[k].im, sj));
+        }
+        const cpx<T> r = rot90<T, INV>(qm);
+        v[m] = pm + r;
+        v[7 - m] = pm - r;
+    }
+}
+
 // Radix 9 as 3 x 3: with n = 3 n1 + n2 and k = k1 + 3 k2, three 3-point DFTs over
 // n1, the twiddles w9^(n2 k1), then three 3-point DFTs over n2.
 template <typename T, bool INV, bool COMP = true>
@@ -259,6 +291,7 @@ __host__ __device__ __forceinline__ void dft(cpx<T>* v) {
     if constexpr (R == 3) dft3<T, INV, COMP>(v);
     if constexpr (R == 4) dft4<T, INV, COMP>(v);
     if constexpr (R == 5) dft5<T, INV, COMP>(v);
+    if constexpr (R == 7) dft7<T, INV, COMP>(v);
     if constexpr (R == 8) dft8<T, INV, COMP>(v);
     if constexpr (R == 9) dft9<T, INV, COMP>(v);
     if constexpr (R == 16) dft16<T, INV, COMP>(v);
@@ -271,7 +304,7 @@ constexpr int kMaxStages = 14;
 struct RadixPlan {
     int n;                  // line length
     int nst;                // number of stages
-    int r[kMaxStages];      // radix of each stage (2, 3, 4, 5, 8 or 16)
+    int r[kMaxStages];      // radix of each stage (2, 3, 4, 5, 7, 8 or 16)
 };
 
 // ------------------------------------------------------------------ accessors
@@ -348,6 +381,7 @@ __device__ __forceinline__ void stage_any(int R, const Src& src, const Dst& dst,
         case 3: stage<T, 3, INV>(src, dst, N, Ns, ncol, tw, tws); break;
         case 4: stage<T, 4, INV>(src, dst, N, Ns, ncol, tw, tws); break;
         case 5: stage<T, 5, INV>(src, dst, N, Ns, ncol, tw, tws); break;
+        case 7: stage<T, 7, INV>(src, dst, N, Ns, ncol, tw, tws); break;
         case 8: stage<T, 8, INV>(src, dst, N, Ns, ncol, tw, tws); break;
         case 16: stage<T, 16, INV>(src, dst, N, Ns, ncol, tw, tws); break;
         default: break;

@@ -36,9 +36,9 @@ int noalloc_fail(int status, const char* msg) {
     return status;
 }
 
-bool smooth235_na(int n) {
+bool smooth_na(int n) {  // 2/3/5/7-smooth
     if (n < 1) return false;
-    for (int p : {2, 3, 5})
+    for (int p : {2, 3, 5, 7})
         while (n % p == 0) n /= p;
     return n == 1;
 }
@@ -46,10 +46,11 @@ bool smooth235_na(int n) {
 bool radix_plan_na(int n, RadixPlan* rp) {
     rp->n = n;
     rp->nst = 0;
-    int e2 = 0, m = n, n3 = 0, n5 = 0;
+    int e2 = 0, m = n, n3 = 0, n5 = 0, n7 = 0;
     while (m % 2 == 0) m /= 2, ++e2;
     while (m % 3 == 0) m /= 3, ++n3;
     while (m % 5 == 0) m /= 5, ++n5;
+    while (m % 7 == 0) m /= 7, ++n7;
     if (m != 1) return false;
     if (e2 > 0) {
         const int st = (e2 + 3) / 4;
@@ -57,6 +58,7 @@ bool radix_plan_na(int n, RadixPlan* rp) {
     }
     for (int i = 0; i < n3; ++i) rp->r[rp->nst++] = 3;
     for (int i = 0; i < n5; ++i) rp->r[rp->nst++] = 5;
+    for (int i = 0; i < n7; ++i) rp->r[rp->nst++] = 7;
     return rp->nst >= 1 && rp->nst <= kMaxStages;
 }
 
@@ -98,8 +100,8 @@ extern "C" int hartree_solve_density_noalloc(const hartree_desc* desc, const voi
     if (d.flags != 0 || (d.precision != HARTREE_FP64 && d.precision != HARTREE_FP32))
         return noalloc_fail(HARTREE_ERR_INVALID, "solve_density_noalloc: precision must be FP64 or FP32, flags 0");
     for (int i = 0; i < 3; ++i) {
-        if (d.n[i] < 2 || d.n[i] > kMaxAxis || !smooth235_na(d.n[i]))
-            return noalloc_fail(HARTREE_ERR_UNSUPPORTED_SIZE, "solve_density_noalloc: a grid size is not 2/3/5-smooth");
+        if (d.n[i] < 2 || d.n[i] > kMaxAxis || !smooth_na(d.n[i]))
+            return noalloc_fail(HARTREE_ERR_UNSUPPORTED_SIZE, "solve_density_noalloc: a grid size is not 2/3/5/7-smooth");
         if (!(d.cell[i] > 0.0) || !std::isfinite(d.cell[i]))
             return noalloc_fail(HARTREE_ERR_INVALID, "solve_density_noalloc: cell sides must be positive");
     }

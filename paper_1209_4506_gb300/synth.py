@@ -161,6 +161,19 @@ def config3b(seed: Optional[int] = None) -> System:
     return System("diamond-ortho 360x384x400 fp32", (360, 384, 400), cell, 0.5, pos, q, "fp32")
 
 
+def config_paper420(seed: Optional[int] = None) -> System:
+    """16x16x8 diamond supercell (16,384 atoms, 107.84 x 107.84 x 53.92 Bohr) on 420 x 420 x 210.
+
+    This is the grid of the paper's memory benchmark of the 16,384-atom diamond system (Sec. 5.2.6),
+    at its spacing of about 0.257 Bohr (the 150 Ry cutoff of Sec. 5.1.1).  Radix 7 on every axis.
+    sigma = 0.8 Bohr keeps the Gaussians resolved at that spacing.  FP32."""
+    rng = rng_for(6, seed)
+    cell = (16 * DIAMOND_A, 16 * DIAMOND_A, 8 * DIAMOND_A)
+    pos = jitter(rng, diamond_supercell((16, 16, 8)), 0.1, cell)
+    q = centred_uniform_charges(rng, pos.shape[0])
+    return System("diamond-16x16x8 420x420x210 fp32", (420, 420, 210), cell, 0.8, pos, q, "fp32")
+
+
 def config4(seed: Optional[int] = None, n_cells: int = 64) -> List[System]:
     """64 independent orthorhombic cells, edges U(8, 30) Bohr, 0.17 Bohr spacing, 8..1000 atoms."""
     rng = rng_for(4, seed)
@@ -206,4 +219,5 @@ CONFIGS = {
     "cfg3a": config3a,
     "cfg3b": config3b,
     "cfg5": config5,
+    "paper420": config_paper420,
 }

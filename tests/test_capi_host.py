@@ -65,7 +65,7 @@ def _desc(n=(32, 32, 32), cell=(6.0, 6.0, 6.0), sigma=0.5, prec=capi.HARTREE_FP3
     "kw,status",
     [
         (dict(n=(32, 32, 33)), capi.HARTREE_ERR_UNSUPPORTED_SIZE),  # odd N3
-        (dict(n=(32, 7, 32)), capi.HARTREE_ERR_UNSUPPORTED_SIZE),  # prime 7
+        (dict(n=(32, 11, 32)), capi.HARTREE_ERR_UNSUPPORTED_SIZE),  # prime 11 (radices are 2, 3, 5, 7)
         (dict(n=(1, 32, 32)), capi.HARTREE_ERR_UNSUPPORTED_SIZE),
         (dict(n=(32, 32, 2)), capi.HARTREE_ERR_UNSUPPORTED_SIZE),
         (dict(n=(8192, 32, 32)), capi.HARTREE_ERR_UNSUPPORTED_SIZE),

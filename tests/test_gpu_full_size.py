@@ -1,8 +1,9 @@
 """Parity at the full workload sizes, in the launch configuration bench.py times.
 
-The 8x8x8 diamond supercell on 512^3 (4,096 Gaussian charges, sigma 0.5 Bohr)
-and the orthorhombic 37.9 x 40.4 x 42.1 Bohr cell on 360 x 384 x 400 (1,728
-atoms): atoms in the order of the modified recursive bisection with 16 atoms
+The 8x8x8 diamond supercell on 512^3 (4,096 Gaussian charges, sigma 0.5 Bohr),
+the orthorhombic 37.9 x 40.4 x 42.1 Bohr cell on 360 x 384 x 400 (1,728
+atoms) and the 16x16x8 supercell on the paper's 420 x 420 x 210 grid (16,384
+atoms, sigma 0.8 Bohr, radix 7): atoms in the order of the modified recursive bisection with 16 atoms
 per leaf, kernel variants picked by the autotuner, and the whole step
 (splat, Poisson solve, E_H, forces) in one hartree_step call, against the
 FP64 oracle on the host cores with the same per-axis cutoff of 5 sigma.
@@ -30,9 +31,9 @@ def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-@pytest.mark.parametrize("name", ["cfg3a", "cfg3b"])
+@pytest.mark.parametrize("name", ["cfg3a", "cfg3b", "paper420"])
 def test_full_size_step_matches_oracle(name):
-    S = {"cfg3a": synth.config3a, "cfg3b": synth.config3b}[name]()
+    S = {"cfg3a": synth.config3a, "cfg3b": synth.config3b, "paper420": synth.config_paper420}[name]()
     O.set_threads(os.cpu_count() or 1)
     rho_o = O.splat(S.n, S.cell, S.sigma, S.pos, S.q, RC_SIGMAS)
     vh_o, eh_o, eh_spec, _ = O.poisson(S.cell, rho_o)

@@ -78,6 +78,8 @@ POISSON_SHAPES = [
     ((4, 4096, 4), (1.0, 400.0, 1.0)),  # largest axis, b
     ((4, 4, 4096), (1.0, 1.0, 400.0)),  # largest axis, c
     ((120, 120, 120), (13.48, 13.48, 13.48)),
+    ((14, 21, 28), (3.0, 4.5, 6.0)),  # radix 7 on every axis
+    ((70, 42, 84), (15.0, 9.0, 18.0)),  # 7 with 2, 3, 5 (c: M = 42)
 ]
 
 

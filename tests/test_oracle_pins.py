@@ -60,7 +60,7 @@ def small_ortho_system(seed=7, nat=5):
 
 
 # ------------------------------------------------------------------ FFT
-@pytest.mark.parametrize("n", [(4, 6, 10), (8, 8, 8), (6, 10, 12), (3, 5, 4), (16, 16, 16)])
+@pytest.mark.parametrize("n", [(4, 6, 10), (8, 8, 8), (6, 10, 12), (3, 5, 4), (16, 16, 16), (7, 6, 14), (14, 21, 4)])
 def test_fft3d_matches_bruteforce_dft(n):
     rng = np.random.default_rng(11)
     x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
@@ -72,7 +72,7 @@ def test_fft3d_matches_bruteforce_dft(n):
     assert np.max(np.abs(fast_inv - brute_inv)) <= 1e-13 * np.max(np.abs(brute_inv))
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 11, 12, 60, 120, 128, 360, 400, 512])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 11, 12, 60, 120, 128, 210, 360, 400, 420, 512])
 def test_fft1d_matches_pocketfft(n):
     rng = np.random.default_rng(n)
     x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
