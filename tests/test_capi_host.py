@@ -197,3 +197,26 @@ def test_split_precision_requires_n2_256():
     h = ctypes.c_void_p()
     assert capi.hartree_plan_create(ctypes.byref(d), ctypes.byref(h)) == capi.HARTREE_ERR_UNSUPPORTED_SIZE
     assert b"N2 = 256" in capi.hartree_last_error()
+
+
+def test_paper_decomposition_experiment_16384_atoms_19_processes():
+    """The experiment of Sec. 5.2.1: 16,384 diamond atoms split over 19 processes by the modified
+    recursive bisection.  Every leaf holds 862 or 863 atoms (w = 1), and the leaves are compact:
+    their mean radius of gyration is within 25% of a cube of the same volume and less than half
+    that of a random 19-way split."""
+    rng = np.random.default_rng(5)
+    cell = (16 * 6.74, 16 * 6.74, 8 * 6.74)
+    pos = synth.jitter(rng, synth.diamond_supercell((16, 16, 8)), 0.1, cell)
+    perm, ls = atoms_reorder(pos, 19)
+    sizes = np.diff(ls)
+    assert sizes.sum() == 16384 and sizes.min() == 862 and sizes.max() == 863
+
+    def rg(p):
+        return np.sqrt(((p - p.mean(0)) ** 2).sum(1).mean())
+
+    r_bis = np.mean([rg(pos[perm[ls[i]:ls[i + 1]]]) for i in range(19)])
+    rnd = np.random.default_rng(0).permutation(len(pos))
+    r_rand = np.mean([rg(pos[rnd[ls[i]:ls[i + 1]]]) for i in range(19)])
+    r_cube = (np.prod(cell) / 19) ** (1 / 3) * np.sqrt(3 / 12)
+    assert r_bis <= 1.25 * r_cube
+    assert r_bis <= 0.5 * r_rand
