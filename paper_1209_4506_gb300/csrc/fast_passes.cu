@@ -739,6 +739,7 @@ bool with_line_stream_cfg(int m, F&& f) {
         case 256: f(LineStreamCfg<16, 256, 16, 16, 1, 2>{}); return true;
         case 512: f(LineStreamCfg<8, 256, 8, 8, 8, 2>{}); return true;
         case 200: f(LineStreamCfg<16, 256, 8, 5, 5, 2>{}); return true;
+        case 105: f(LineStreamCfg<16, 256, 3, 5, 7, 2>{}); return true;
         default: return false;
     }
 }
@@ -812,6 +813,10 @@ bool with_col_tma_cfg(int n, int variant, F&& f) {
             if (variant == 1) f(ColTmaCfg<256, 16, 8, 3, 3, 8, 2>{});
             else f(ColTmaCfg<512, 16, 8, 3, 3>{});
             return true;
+        case 420:
+            if (variant == 1) f(ColTmaCfg<256, 12, 5, 7, 2, 8, 3>{});
+            else f(ColTmaCfg<256, 12, 5, 7, 3, 8, 2>{});
+            return true;
         default: return false;
     }
 }
@@ -838,12 +843,15 @@ bool with_col_cfg(int n, int variant, F&& f) {
             return true;
         case 1024: f(ColCfg<T, 8, 512, 16, 8, 8>{}); return true;
         case 360: f(ColCfg<T, d ? 8 : 16, 256, 8, 5, 9>{}); return true;
+        case 420: f(ColCfg<T, 8, 256, 12, 5, 7>{}); return true;
         case 384: f(ColCfg<T, d ? 8 : 16, d ? 256 : 512, 16, 8, 3>{}); return true;
         default: return false;
     }
 }
 int col_variants(int n) { return (n == 256 || n == 512) ? 2 : 1; }
-int col_tma_variants(int n) { return n == 512 ? 6 : (n == 256 ? 3 : (n == 360 ? 3 : (n == 384 ? 2 : 0))); }
+int col_tma_variants(int n) {
+    return n == 512 ? 6 : (n == 256 ? 3 : (n == 360 ? 3 : (n == 384 || n == 420 ? 2 : 0)));
+}
 
 // Variants col_variants(n) .. of the b / a passes: the TMA-streamed kernels (FP32, plan has the tensor maps).
 bool col_tma_available(const Plan& p, int axis) {
@@ -872,6 +880,7 @@ bool with_line_cfg(int m, int variant, F&& f) {
             return true;
         case 1024: f(LineCfg<T, 4, 256, 16, 8, 8>{}); return true;
         case 200: f(LineCfg<T, 16, 256, 8, 5, 5>{}); return true;
+        case 105: f(LineCfg<T, 16, 256, 3, 5, 7>{}); return true;
         default: return false;
     }
 }
@@ -880,8 +889,13 @@ int line_variants(int m) { return (m == 128 || m == 256 || m == 512) ? 2 : 1; }
 // Variant line_variants(M) of the c passes: the bulk-streamed kernels (FP32; the plan's
 // row stride and the caller's grid pointers must allow 16-byte bulk copies).
 bool line_stream_available(const Plan& p) {
-    return p.prec != HARTREE_FP64 && p.d_err != nullptr && p.sm_count > 0 && (p.ldc * 8) % 16 == 0 &&
-           with_line_stream_cfg(p.M, [](auto) {});
+    int lines = 0;
+    if (p.prec == HARTREE_FP64 || p.d_err == nullptr || p.sm_count <= 0 || (p.ldc * 8) % 16 != 0 ||
+        !with_line_stream_cfg(p.M, [&](auto c) { lines = c.lines; }))
+        return false;
+    // every bulk copy of rho (lines of 8 M bytes) must be a multiple of 16 bytes: M even, or
+    // whole tiles only (LINES even)
+    return p.M % 2 == 0 || ((long long)p.n[0] * p.n[1]) % lines == 0;
 }
 
 template <typename T>

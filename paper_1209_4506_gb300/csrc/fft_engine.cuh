@@ -183,6 +183,36 @@ __host__ __device__ __forceinline__ void dft7(cpx<T>* v) {
     }
 }
 
+// Radix 12 as 4 x 3: with n = 3 n1 + n2 and k = k1 + 4 k2, three 4-point DFTs over
+// n1, the twiddles w12^(n2 k1), then four 3-point DFTs over n2.
+template <typename T, bool INV, bool COMP = true>
+__host__ __device__ __forceinline__ void dft12(cpx<T>* v) {
+    const double h = 0.866025403784438646764;  // cos(pi / 6) = sin(pi / 3)
+    const double sg = INV ? 1.0 : -1.0;
+    cpx<T> y[3][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2) {
+        cpx<T> t[4] = {v[n2], v[n2 + 3], v[n2 + 6], v[n2 + 9]};
+        dft4<T, INV, COMP>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = t[k1];
+    }
+    y[1][1] = kcmul<T, COMP>(y[1][1], h, sg * 0.5);  // w12^1
+    y[1][2] = kcmul<T, COMP>(y[1][2], 0.5, sg * h);  // w12^2
+    y[1][3] = rot90<T, INV>(y[1][3]);                // w12^3
+    y[2][1] = kcmul<T, COMP>(y[2][1], 0.5, sg * h);  // w12^2
+    y[2][2] = kcmul<T, COMP>(y[2][2], -0.5, sg * h);  // w12^4
+    y[2][3] = mk(-y[2][3].re, -y[2][3].im);          // w12^6
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        cpx<T> t[3] = {y[0][k1], y[1][k1], y[2][k1]};
+        dft3<T, INV, COMP>(t);
+        v[k1] = t[0];
+        v[k1 + 4] = t[1];
+        v[k1 + 8] = t[2];
+    }
+}
+
 // Radix 9 as 3 x 3: with n = 3 n1 + n2 and k = k1 + 3 k2, three 3-point DFTs over
 // n1, the twiddles w9^(n2 k1), then three 3-point DFTs over n2.
 template <typename T, bool INV, bool COMP = true>
@@ -294,6 +324,7 @@ __host__ __device__ __forceinline__ void dft(cpx<T>* v) {
     if constexpr (R == 7) dft7<T, INV, COMP>(v);
     if constexpr (R == 8) dft8<T, INV, COMP>(v);
     if constexpr (R == 9) dft9<T, INV, COMP>(v);
+    if constexpr (R == 12) dft12<T, INV, COMP>(v);
     if constexpr (R == 16) dft16<T, INV, COMP>(v);
     if constexpr (R == 32) dft32<T, INV, COMP>(v);
 }

@@ -275,7 +275,8 @@ def test_single_passes_reproduce_solve_density(precision):
 
 @pytest.mark.parametrize(
     "shape,precision",
-    [((512, 256, 512), "fp32"), ((256, 512, 256), "fp32"), ((256, 512, 256), "fp64"), ((360, 384, 400), "fp32")],
+    [((512, 256, 512), "fp32"), ((256, 512, 256), "fp32"), ((256, 512, 256), "fp64"), ((360, 384, 400), "fp32"),
+     ((420, 420, 210), "fp32")],
 )
 def test_kernel_variants_agree(shape, precision):
     """Every compiled variant of every pass kind (tile shapes, thread counts, radix orders,
@@ -331,6 +332,7 @@ def test_kernel_variants_agree(shape, precision):
      ((3, 10, 512), (0.8, 2.0, 60.0)),  # M = 256: 30 lines, tiles of 16 (last tile 14 lines)
      ((3, 5, 1024), (0.7, 1.0, 110.0)),  # M = 512: 15 lines, tiles of 8
      ((3, 10, 400), (0.8, 2.0, 42.0)),  # M = 200 (radices 8, 5, 5): 30 lines, tiles of 16
+     ((3, 16, 210), (0.8, 3.0, 27.0)),  # M = 105 (odd; radices 3, 5, 7): 48 lines, whole tiles only
      ((512, 64, 512), (60.0, 8.0, 60.0))],  # 2,048 tiles: every ring slot reused many times
 )
 def test_streamed_c_passes_equal_plain_kernels(shape, cell):
@@ -348,7 +350,7 @@ def test_streamed_c_passes_equal_plain_kernels(shape, cell):
     rho = torch.tensor(rho32, device="cuda")
     plan.set_variants([0, 0, 0])
     v0, e0 = plan.solve_density(rho)
-    plan.set_variants([1 if shape[2] == 400 else 2, 0, 0])  # the streamed c passes
+    plan.set_variants([1 if shape[2] in (400, 210) else 2, 0, 0])  # the streamed c passes
     v2, e2 = plan.solve_density(rho)
     torch.cuda.synchronize()
     plan.device_status()
