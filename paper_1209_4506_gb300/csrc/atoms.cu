@@ -265,7 +265,7 @@ __host__ __device__ __forceinline__ int ring_offset(int ld) {
 // arithmetic: each thread keeps kDepth slices of its pairs in flight with
 // cp.async copies into a private ring in shared memory.
 template <typename T, int VW, int KP>
-__global__ void __launch_bounds__(kThreads) k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs,
+__global__ void __launch_bounds__(kThreads, KP <= 2 ? 4 : 3) k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs,
                                                      double* __restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int fb = a.fb;
