@@ -515,8 +515,8 @@ __device__ __forceinline__ void drain_ring(uint64_t* mbar, int k, int ntiles, in
     }
 }
 
-template <int LINES, int NT, int R0, int R1, int R2, int NBUF>
-__global__ void __launch_bounds__(NT, 2)
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_r2c_stream(const float* __restrict__ rho, FastArgs<float> a, int ntiles, int* err) {
     constexpr int M = R0 * R1 * R2;
     constexpr int N = M;
@@ -594,8 +594,9 @@ __global__ void __launch_bounds__(NT, 2)
     }
 }
 
-template <int LINES, int NT, int R0, int R1, int R2, int NBUF>
-__global__ void __launch_bounds__(NT, 2) k_c2r_stream(float* __restrict__ vout, FastArgs<float> a, int ntiles, int* err) {
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_c2r_stream(float* __restrict__ vout, FastArgs<float> a, int ntiles, int* err) {
     constexpr int M = R0 * R1 * R2;
     constexpr int N = M;
     constexpr int TPL = NT / LINES;
@@ -696,8 +697,9 @@ struct LineCfg {
     }
 };
 
-// Bulk-streamed c-pass configuration (FP32): LINES lines per tile, NBUF ring slots, two CTAs per SM.
-template <int LINES, int NT, int R0, int R1, int R2, int NBUF>
+// Bulk-streamed c-pass configuration (FP32): LINES lines per tile, NBUF ring slots, MINB CTAs per SM
+// (fewer where they do not fit).
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB = 2>
 struct LineStreamCfg {
     static constexpr int lines = LINES, m = R0 * R1 * R2;
     static size_t smem_work() { return (size_t)LINES * (m + m / 16 + 1) * sizeof(cpx<float>) + NBUF * 8; }
@@ -710,39 +712,57 @@ struct LineStreamCfg {
     static size_t smem() { return 0; }  // checked per kernel in configure()
     static cudaError_t configure(int optin) {
         cudaError_t e;
-        if ((e = allow_max_dynamic_smem(k_r2c_stream<LINES, NT, R0, R1, R2, NBUF>, optin))) return e;
-        return allow_max_dynamic_smem(k_c2r_stream<LINES, NT, R0, R1, R2, NBUF>, optin);
+        if ((e = allow_max_dynamic_smem(k_r2c_stream<LINES, NT, R0, R1, R2, NBUF, MINB>, optin))) return e;
+        return allow_max_dynamic_smem(k_c2r_stream<LINES, NT, R0, R1, R2, NBUF, MINB>, optin);
+    }
+    // CTAs per SM the persistent grid relies on: MINB, or fewer if they do not fit
+    static int resident(bool inverse, size_t need) {
+        int b = 0;
+        const cudaError_t e =
+            inverse ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          &b, k_c2r_stream<LINES, NT, R0, R1, R2, NBUF, MINB>, NT, need)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          &b, k_r2c_stream<LINES, NT, R0, R1, R2, NBUF, MINB>, NT, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return 1;
+        }
+        return b < 1 ? 1 : (b < MINB ? b : MINB);
     }
     static long long launch(bool inverse, int sm_count, const void* in, void* out, const FastArgs<float>& a,
                             int* err, cudaStream_t s) {
         const long long nlines = (long long)a.n1 * a.n2;
         const int ntiles = (int)((nlines + LINES - 1) / LINES);
-        // two CTAs per SM where both fit in the SM's 228 KB of shared memory (1 KB reserved per CTA)
         const size_t need = inverse ? smem_c2r(a.ldc) : smem_r2c();
-        int grid = (2 * (need + 1024) <= 228 * 1024 ? 2 : 1) * sm_count;
+        int grid = resident(inverse, need) * sm_count;
         if (grid > ntiles) grid = ntiles;
         if (!inverse)
-            k_r2c_stream<LINES, NT, R0, R1, R2, NBUF>
-                <<<grid, NT, smem_r2c(), s>>>(static_cast<const float*>(in), a, ntiles, err);
+            k_r2c_stream<LINES, NT, R0, R1, R2, NBUF, MINB>
+                <<<grid, NT, need, s>>>(static_cast<const float*>(in), a, ntiles, err);
         else
-            k_c2r_stream<LINES, NT, R0, R1, R2, NBUF>
-                <<<grid, NT, smem_c2r(a.ldc), s>>>(static_cast<float*>(out), a, ntiles, err);
+            k_c2r_stream<LINES, NT, R0, R1, R2, NBUF, MINB>
+                <<<grid, NT, need, s>>>(static_cast<float*>(out), a, ntiles, err);
         return grid;
     }
 };
 
 // Streamed c passes by M = N3 / 2 (tiles of 32 KB of rho).
+// Variant 1 (where it exists): one ring slot, three CTAs per SM.
 template <class F>
-bool with_line_stream_cfg(int m, F&& f) {
+bool with_line_stream_cfg(int m, int variant, F&& f) {
     switch (m) {
         case 128: f(LineStreamCfg<32, 256, 16, 8, 1, 2>{}); return true;
-        case 256: f(LineStreamCfg<16, 256, 16, 16, 1, 2>{}); return true;
+        case 256:
+            if (variant == 1) f(LineStreamCfg<16, 256, 16, 16, 1, 1, 3>{});
+            else f(LineStreamCfg<16, 256, 16, 16, 1, 2>{});
+            return true;
         case 512: f(LineStreamCfg<8, 256, 8, 8, 8, 2>{}); return true;
         case 200: f(LineStreamCfg<16, 256, 8, 5, 5, 2>{}); return true;
         case 105: f(LineStreamCfg<16, 256, 3, 5, 7, 2>{}); return true;
         default: return false;
     }
 }
+int line_stream_variants(int m) { return m == 256 ? 2 : (with_line_stream_cfg(m, 0, [](auto) {}) ? 1 : 0); }
 
 // TMA-streamed column pass configuration (FP32): COLS columns (16: 128-byte rows, one CTA per
 // SM; 8: 64-byte rows, MINB CTAs per SM, each with its own barriers) per tile.
@@ -891,7 +911,7 @@ int line_variants(int m) { return (m == 128 || m == 256 || m == 512) ? 2 : 1; }
 bool line_stream_available(const Plan& p) {
     int lines = 0;
     if (p.prec == HARTREE_FP64 || p.d_err == nullptr || p.sm_count <= 0 || (p.ldc * 8) % 16 != 0 ||
-        !with_line_stream_cfg(p.M, [&](auto c) { lines = c.lines; }))
+        !with_line_stream_cfg(p.M, 0, [&](auto c) { lines = c.lines; }))
         return false;
     // every bulk copy of rho (lines of 8 M bytes) must be a multiple of 16 bytes: M even, or
     // whole tiles only (LINES even)
@@ -949,11 +969,12 @@ cudaError_t configure_fast_t(const Plan& p, int optin) {
     for (int v = 0; v < line_variants(p.M); ++v) with_line_cfg<T>(p.M, v, cfg);
     if constexpr (sizeof(T) == 4) {
         if (line_stream_available(p))
-            with_line_stream_cfg(p.M, [&](auto c) {
-                const size_t need = std::max(c.smem_r2c(), c.smem_c2r(p.ldc));
-                if (e == cudaSuccess && need + 2048 > (size_t)optin) e = cudaErrorInvalidConfiguration;
-                if (e == cudaSuccess) e = c.configure(optin);
-            });
+            for (int v = 0; v < line_stream_variants(p.M); ++v)
+                with_line_stream_cfg(p.M, v, [&](auto c) {
+                    const size_t need = std::max(c.smem_r2c(), c.smem_c2r(p.ldc));
+                    if (e == cudaSuccess && need + 2048 > (size_t)optin) e = cudaErrorInvalidConfiguration;
+                    if (e == cudaSuccess) e = c.configure(optin);
+                });
     }
     for (int v = 0; v < col_variants(p.n[1]); ++v) with_col_cfg<T>(p.n[1], v, cfg);
     for (int v = 0; v < col_variants(p.n[0]); ++v) with_col_cfg<T>(p.n[0], v, cfg);
@@ -981,9 +1002,9 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
     if (pass == 0 || pass == 4) {
         if constexpr (sizeof(T) == 4) {
             const void* grid_ptr = pass == 0 ? rho : vh;
-            if (p.var[0] == line_variants(p.M) && line_stream_available(p) &&
-                reinterpret_cast<uintptr_t>(grid_ptr) % 16 == 0) {
-                with_line_stream_cfg(p.M, [&](auto c) {
+            const int sv = p.var[0] - line_variants(p.M);
+            if (sv >= 0 && line_stream_available(p) && reinterpret_cast<uintptr_t>(grid_ptr) % 16 == 0) {
+                with_line_stream_cfg(p.M, sv, [&](auto c) {
                     grid = c.launch(pass == 4, p.sm_count, rho, vh, a, p.d_err, s);
                 });
                 return grid;
@@ -1028,7 +1049,8 @@ long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, c
 }
 
 int fast_variants(const Plan& p, int kind) {
-    if (kind == 0) return (p.use_fast & 1) ? line_variants(p.M) + (line_stream_available(p) ? 1 : 0) : 1;
+    if (kind == 0)
+        return (p.use_fast & 1) ? line_variants(p.M) + (line_stream_available(p) ? line_stream_variants(p.M) : 0) : 1;
     const int ax = kind == 1 ? 1 : 0;
     if (!(p.use_fast & (kind == 1 ? 2 : 4))) return 1;
     return col_variants(p.n[ax]) + (col_tma_available(p, ax) ? col_tma_variants(p.n[ax]) : 0);
