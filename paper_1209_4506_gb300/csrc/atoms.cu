@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int
 // is that of the leaf-selecting splat, then factors are staged in batches and
 // accumulated as there.  Longer lists take the leaf-selecting path.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 4) k_splat_binned(AtomArgs<T> a, T* __restrict__ rho, int tiles_b,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 4) k_splat_binned(AtomArgs<T> a, T* __restrict__ rho, int tiles_b,
                                                            int tiles_c, const int* __restrict__ cursor,
                                                            const int4* __restrict__ list) {
     __shared__ int4 ent[kBinCap];
