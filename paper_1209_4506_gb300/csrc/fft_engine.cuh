@@ -373,21 +373,28 @@ struct GlobalTile {
     __device__ __forceinline__ void st_(int col, int n, cpx<T> v) const { p[(long long)n * sn + col] = v; }
 };
 
+// x / d by a multiply-high with m = ceil(2^32 / d) (m = 0 marks d = 1).  Exact when
+// x (m d - 2^32) < 2^32, which holds for x < 2^20 and d <= 4096.
+__device__ __forceinline__ uint32_t fdiv_magic(uint32_t d) { return d <= 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, uint32_t m) { return m == 0u ? x : __umulhi(x, m); }
+
 // One Stockham stage over a tile.  tw[e * tws] = exp(-2 pi i e / N) for the
-// line length N (tws > 1 when the table belongs to a longer line).
+// line length N (tws > 1 when the table belongs to a longer line).  The index
+// divisions by the run-time ncol and Ns use precomputed multiply-high constants.
 template <typename T, int R, bool INV, class Src, class Dst>
 __device__ __forceinline__ void stage(const Src& src, const Dst& dst, int N, int Ns, int ncol,
                                       const cpx<T>* __restrict__ tw, int tws) {
     const int nb = N / R;
     const int total = nb * ncol;
     const int tstep = N / (Ns * R);
+    const uint32_t mc = fdiv_magic((uint32_t)ncol), ms = fdiv_magic((uint32_t)Ns);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int col = t % ncol;
-        const int j = t / ncol;
+        const int j = (int)fdiv((uint32_t)t, mc);
+        const int col = t - j * ncol;
         cpx<T> v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src.ld_(col, j + r * nb);
-        const int k = j % Ns;
+        const int k = j - (int)fdiv((uint32_t)j, ms) * Ns;
         if (Ns > 1) {
             const int base = k * tstep;
 #pragma unroll

@@ -12,6 +12,7 @@ namespace hartree {
 template <typename T, bool CG>
 __device__ void c_r2c_tile(const T* __restrict__ rho, const PoissonArgs<T>& a, int tile, unsigned char* smem_raw) {
     const int L = a.c_lines, ld = L + 1, M = a.M;
+    const uint32_t mM = fdiv_magic((uint32_t)M), mM1 = fdiv_magic((uint32_t)(M + 1));
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* B = A + (size_t)(M + 1) * ld;
     const long long nlines = (long long)a.n1 * a.n2;
@@ -19,7 +20,7 @@ __device__ void c_r2c_tile(const T* __restrict__ rho, const PoissonArgs<T>& a, i
     const int nl = (int)min((long long)L, nlines - line0);
     // z[n] = rho[2n] + i rho[2n+1]: coalesced along the line, transposed into [n][line]
     for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-        const int l = e / M, n = e - l * M;
+        const int l = (int)fdiv((uint32_t)e, mM), n = e - l * M;
         const cpx<T>* src = reinterpret_cast<const cpx<T>*>(rho + (line0 + l) * a.n3);
         A[n * ld + l] = gload<CG>(src + n);
     }
@@ -28,7 +29,7 @@ __device__ void c_r2c_tile(const T* __restrict__ rho, const PoissonArgs<T>& a, i
     // X[k] = E[k] + w^k O[k],  E = (Z[k] + conj Z[M-k]) / 2,  O = (Z[k] - conj Z[M-k]) / 2i,  k = 0..M
     const T half = T(0.5);
     for (int e = threadIdx.x; e < nl * (M + 1); e += blockDim.x) {
-        const int l = e / (M + 1), k = e - l * (M + 1);
+        const int l = (int)fdiv((uint32_t)e, mM1), k = e - l * (M + 1);
         const cpx<T> z1 = Z[(k == M ? 0 : k) * ld + l];
         const cpx<T> z2 = conjg(Z[(k == 0 ? 0 : M - k) * ld + l]);
         const cpx<T> E = scale(z1 + z2, half);
@@ -47,6 +48,7 @@ __device__ void b_tile(const PoissonArgs<T>& a, int tile, unsigned char* smem_ra
     const int ia = tile / a.b_chunks;
     const int c0 = (tile - ia * a.b_chunks) * CB;
     const int nc = min(CB, a.nh - c0);
+    const uint32_t mnc = fdiv_magic((uint32_t)nc);
     GlobalTile<T, CG> g{a.W + (long long)ia * a.n2 * a.ldc + c0, a.ldc};
     if (a.rpb.nst >= 2) {
         run_fft<T, INV>(a.rpb, g, g, A, B, CB, nc, a.twb, 1);
@@ -54,7 +56,7 @@ __device__ void b_tile(const PoissonArgs<T>& a, int tile, unsigned char* smem_ra
         // one stage reads and writes different rows: go through shared memory
         cpx<T>* F = run_fft_to_smem<T, INV>(a.rpb, g, A, B, CB, nc, a.twb, 1);
         for (int e = threadIdx.x; e < a.n2 * nc; e += blockDim.x) {
-            const int col = e % nc, n = e / nc;
+            const int n = (int)fdiv((uint32_t)e, mnc), col = e - n * nc;
             g.st_(col, n, F[n * CB + col]);
         }
     }
@@ -71,13 +73,14 @@ __device__ void a_green_tile(const PoissonArgs<T>& a, int tile, int part_index, 
     const int ib = tile / a.a_chunks;
     const int c0 = (tile - ib * a.a_chunks) * CA;
     const int nc = min(CA, a.nh - c0);
+    const uint32_t mnc = fdiv_magic((uint32_t)nc);
     GlobalTile<T, CG> g{a.W + (long long)ib * a.ldc + c0, (long long)a.n2 * a.ldc};
     cpx<T>* F = run_fft_to_smem<T, false>(a.rpa, g, A, B, CA, nc, a.twa, 1);
     // F[k1][col] now holds rho~(k1, ib, c0 + col).
     const cpx<T> gb = a.gsqb[ib];
     T sum = T(0), comp = T(0);  // compensated per-thread partial of sum m |rho~|^2 / G^2
     for (int e = threadIdx.x; e < a.n1 * nc; e += blockDim.x) {
-        const int col = e % nc, k1 = e / nc;
+        const int k1 = (int)fdiv((uint32_t)e, mnc), col = e - k1 * nc;
         const int k3 = c0 + col;
         const cpx<T> v = F[k1 * CA + col];
         // |G|^2 from the split tables: the high parts sum to within one rounding,
@@ -103,19 +106,20 @@ __device__ void a_green_tile(const PoissonArgs<T>& a, int tile, int part_index, 
 template <typename T, bool CG>
 __device__ void c_c2r_tile(T* __restrict__ out, const PoissonArgs<T>& a, int tile, unsigned char* smem_raw) {
     const int L = a.c_lines, ld = L + 1, M = a.M;
+    const uint32_t mM = fdiv_magic((uint32_t)M), mM1 = fdiv_magic((uint32_t)(M + 1));
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* B = A + (size_t)(M + 1) * ld;
     const long long nlines = (long long)a.n1 * a.n2;
     const long long line0 = (long long)tile * L;
     const int nl = (int)min((long long)L, nlines - line0);
     for (int e = threadIdx.x; e < nl * (M + 1); e += blockDim.x) {
-        const int l = e / (M + 1), k = e - l * (M + 1);
+        const int l = (int)fdiv((uint32_t)e, mM1), k = e - l * (M + 1);
         A[k * ld + l] = gload<CG>(a.W + (line0 + l) * a.ldc + k);
     }
     __syncthreads();
     // Z[k] = (X[k] + conj X[M-k]) + i w^-k (X[k] - conj X[M-k]),  k < M
     for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-        const int l = e / M, k = e - l * M;
+        const int l = (int)fdiv((uint32_t)e, mM), k = e - l * M;
         const cpx<T> x1 = A[k * ld + l];
         const cpx<T> x2 = conjg(A[(M - k) * ld + l]);
         const cpx<T> Ep = x1 + x2;
@@ -125,7 +129,7 @@ __device__ void c_c2r_tile(T* __restrict__ out, const PoissonArgs<T>& a, int til
     __syncthreads();
     cpx<T>* z = run_fft_to_smem<T, true>(a.rpc, SmemTile<T>{B, ld}, A, B, ld, nl, a.twc, 2);
     for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-        const int l = e / M, n = e - l * M;
+        const int l = (int)fdiv((uint32_t)e, mM), n = e - l * M;
         reinterpret_cast<cpx<T>*>(out + (line0 + l) * a.n3)[n] = z[n * ld + l];
     }
 }
