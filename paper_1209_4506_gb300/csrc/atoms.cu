@@ -251,41 +251,16 @@ __host__ __device__ __forceinline__ int ring_offset(int ld) {
     return (int)(((size_t)6 * ld * sizeof(T) + 15) / 16 * 16 / sizeof(T));
 }
 
-// Force gather of one atom (or a slab of its a range) per CTA.
-//
-// V is periodic, so sum_m fac[m] V[(lo + m) mod n] = sum_t w[t] V[(lo + t) mod n]
-// over the min(cnt, n) distinct wrapped indices t, with the image-summed weight
-// w[t] = sum_{m = t (mod n), m < cnt} fac[m] (likewise for dfac).  Shared memory
-// holds these weights for the three axes; the c axis is laid out in slots of VW
-// starting at the VW-aligned wrapped index below the box, zero outside it, so
-// each (b row, c group) pair is one aligned vector load.  Per a slice a thread
-// contracts its KP pairs: r0 = sum_e V_e wc_e, r1 = sum_e V_e dwc_e, then
-// p0 += wb r0, py += dwb r0, pz += wb r1; slices are combined with wa / dwa in
-// compensated sums.  The gather is bound by loads in flight, not by
-// arithmetic: each thread keeps kDepth slices of its pairs in flight with
-// cp.async copies into a private ring in shared memory.
-template <typename T, int VW, int KP>
-__global__ void __launch_bounds__(kThreads, KP <= 2 ? 4 : 3) k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs,
-                                                     double* __restrict__ part) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int fb = a.fb;
-    const int ld = fb + 8;
-    T* wf = reinterpret_cast<T*>(smem_raw);  // [3][ld] image-summed fac (c axis: per slot)
-    T* wd = wf + 3 * ld;                     // [3][ld] image-summed dfac
-    __shared__ double red[4][kThreads / 32];
-    const int atom = blockIdx.x / slabs, slab = blockIdx.x - atom * slabs;
-    const AtomPrep<T> p = a.prep[atom];
-    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
-    int nw[3], st[3];
-    nw[0] = min(p.cnt[0], n1), nw[1] = min(p.cnt[1], n2), nw[2] = min(p.cnt[2], n3);
-    st[0] = imod(p.lo[0], n1), st[1] = imod(p.lo[1], n2), st[2] = imod(p.lo[2], n3);
-    const int lead = st[2] % VW;  // VW divides n3
-    const int cst = st[2] - lead;
-    const int nslot = (lead + nw[2] + VW - 1) / VW * VW;
-    const int ng = nslot / VW;
+// Image-summed weights of one atom's box in shared memory: wf[d][slot] = sum over the box
+// points m that land on wrapped index t of fac[m] (dfac in wd), for t < nw[d]; the c axis is
+// laid out in slots from the VW-aligned index below the box (slot = t + lead), zero outside.
+template <typename T>
+__device__ __forceinline__ void forces_weights(const AtomArgs<T>& a, const AtomPrep<T>& p, int atom, const int* nw,
+                                               int lead, int nslot, T* wf, T* wd, int ld) {
+    const int fb = a.fb, n1 = a.n1, n2 = a.n2, n3 = a.n3;
     const T* F = a.fac + (long long)atom * 3 * fb;
     const T* DF = a.dfac + (long long)atom * 3 * fb;
-    for (int e = threadIdx.x; e < nw[0] + nw[1] + nslot; e += kThreads) {
+    for (int e = threadIdx.x; e < nw[0] + nw[1] + nslot; e += blockDim.x) {
         int d, t, slot;
         if (e < nw[0]) {
             d = 0, t = e, slot = e;
@@ -306,6 +281,41 @@ __global__ void __launch_bounds__(kThreads, KP <= 2 ? 4 : 3) k_forces(AtomArgs<T
         wf[d * ld + slot] = s;
         wd[d * ld + slot] = sd;
     }
+}
+
+// Force gather of one atom (or a slab of its a range) per CTA.
+//
+// V is periodic, so sum_m fac[m] V[(lo + m) mod n] = sum_t w[t] V[(lo + t) mod n]
+// over the min(cnt, n) distinct wrapped indices t, with the image-summed weight
+// w[t] = sum_{m = t (mod n), m < cnt} fac[m] (likewise for dfac).  Shared memory
+// holds these weights for the three axes; the c axis is laid out in slots of VW
+// starting at the VW-aligned wrapped index below the box, zero outside it, so
+// each (b row, c group) pair is one aligned vector load.  Per a slice a thread
+// contracts its KP pairs: r0 = sum_e V_e wc_e, r1 = sum_e V_e dwc_e, then
+// p0 += wb r0, py += dwb r0, pz += wb r1; slices are combined with wa / dwa in
+// compensated sums.  The gather is bound by loads in flight, not by
+// arithmetic: each thread keeps kDepth slices of its pairs in flight with
+// cp.async copies into a private ring in shared memory.
+template <typename T, int VW, int KP, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ? 4 : 3)) k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs,
+                                                     double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int fb = a.fb;
+    const int ld = fb + 8;
+    T* wf = reinterpret_cast<T*>(smem_raw);  // [3][ld] image-summed fac (c axis: per slot)
+    T* wd = wf + 3 * ld;                     // [3][ld] image-summed dfac
+    __shared__ double red[4][NT / 32];
+    const int atom = blockIdx.x / slabs, slab = blockIdx.x - atom * slabs;
+    const AtomPrep<T> p = a.prep[atom];
+    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+    int nw[3], st[3];
+    nw[0] = min(p.cnt[0], n1), nw[1] = min(p.cnt[1], n2), nw[2] = min(p.cnt[2], n3);
+    st[0] = imod(p.lo[0], n1), st[1] = imod(p.lo[1], n2), st[2] = imod(p.lo[2], n3);
+    const int lead = st[2] % VW;  // VW divides n3
+    const int cst = st[2] - lead;
+    const int nslot = (lead + nw[2] + VW - 1) / VW * VW;
+    const int ng = nslot / VW;
+    forces_weights(a, p, atom, nw, lead, nslot, wf, wd, ld);
     __syncthreads();
     const int ia0 = (int)((long long)nw[0] * slab / slabs), ia1 = (int)((long long)nw[0] * (slab + 1) / slabs);
     const long long slice = (long long)n2 * n3;
@@ -313,12 +323,12 @@ __global__ void __launch_bounds__(kThreads, KP <= 2 ? 4 : 3) k_forces(AtomArgs<T
     const T* wa = wf;
     const T* dwa = wd;
     T s0 = T(0), c0 = T(0), sx = T(0), cx = T(0), sy = T(0), cy = T(0), sz = T(0), cz = T(0);
-    if (npairs <= kThreads * KP) {
+    if (npairs <= NT * KP) {
         int off[KP];  // b n3 + c of the pair's first point (< 2^24); pairs past the end read point 0 with zero weight
         T wb[KP], dwb[KP], wc[KP][VW], dwc[KP][VW];
 #pragma unroll
         for (int u = 0; u < KP; ++u) {
-            const int pr = threadIdx.x + kThreads * u;
+            const int pr = threadIdx.x + NT * u;
             const bool ok = pr < npairs;
             const int j = ok ? pr / ng : 0, g = ok ? pr - j * ng : 0;
             int bj = st[1] + j;
@@ -343,8 +353,8 @@ __global__ void __launch_bounds__(kThreads, KP <= 2 ? 4 : 3) k_forces(AtomArgs<T
             const T* Vs = V + ai * slice;
 #pragma unroll
             for (int u = 0; u < KP; ++u) {
-                const bool ok = threadIdx.x + kThreads * u < npairs;
-                cp_async<VW * sizeof(T)>(ring + ((slot * KP + u) * kThreads + threadIdx.x) * VW, Vs + off[u],
+                const bool ok = threadIdx.x + NT * u < npairs;
+                cp_async<VW * sizeof(T)>(ring + ((slot * KP + u) * NT + threadIdx.x) * VW, Vs + off[u],
                                          ok ? (int)(VW * sizeof(T)) : 0);
             }
         };
@@ -358,13 +368,13 @@ __global__ void __launch_bounds__(kThreads, KP <= 2 ? 4 : 3) k_forces(AtomArgs<T
             if (t + kDepth - 1 < ia1) issue(t + kDepth - 1, (k + kDepth - 1) % kDepth);
             cp_async_commit();
             cp_async_wait<kDepth - 1>();  // the group of slice t is complete
-            const T* r = ring + (k % kDepth) * KP * kThreads * VW;
+            const T* r = ring + (k % kDepth) * KP * NT * VW;
             T p0 = T(0), py = T(0), pz = T(0);
 #pragma unroll
             for (int u = 0; u < KP; ++u) {
                 T v[VW];
 #pragma unroll
-                for (int e = 0; e < VW; ++e) v[e] = r[(u * kThreads + threadIdx.x) * VW + e];
+                for (int e = 0; e < VW; ++e) v[e] = r[(u * NT + threadIdx.x) * VW + e];
                 T r0 = T(0), r1 = T(0);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
@@ -388,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, KP <= 2 ? 4 : 3) k_forces(AtomArgs<T
             if (ai >= n1) ai -= n1;
             const T* Vs = V + ai * slice;
             T p0 = T(0), py = T(0), pz = T(0);
-            for (int pr = threadIdx.x; pr < npairs; pr += kThreads) {
+            for (int pr = threadIdx.x; pr < npairs; pr += NT) {
                 const int j = pr / ng, g = pr - j * ng;
                 int bj = st[1] + j;
                 if (bj >= n2) bj -= n2;
@@ -463,23 +473,41 @@ cudaError_t splat_impl(const Plan& p, const double* pos, const double* q, int n,
     return cudaGetLastError();
 }
 
-size_t forces_smem(const Plan& p, size_t real_size, int vw, int kp);
-int forces_kp(const Plan& p, int vw);
+// CTA size and pairs per thread of the force gather for the largest box of the plan.
+struct ForceShape {
+    int nt, kp;
+};
+ForceShape forces_shape(const Plan& p, int vw);
+size_t forces_smem(const Plan& p, size_t real_size, int vw, ForceShape fs);
+
+template <typename T, int VW, int NT>
+void launch_k_forces_nt(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs, int kp,
+                        size_t sm, cudaStream_t s) {
+    if constexpr (NT == 128) {
+        switch (kp) {
+            case 5: k_forces<T, VW, 5, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); return;
+            case 6: k_forces<T, VW, 6, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); return;
+            default: break;
+        }
+    }
+    switch (kp) {
+        case 1: k_forces<T, VW, 1, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); break;
+        case 2: k_forces<T, VW, 2, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); break;
+        case 3: k_forces<T, VW, 3, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); break;
+        default: k_forces<T, VW, 4, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); break;
+    }
+}
 
 // Pairs per thread: enough for the largest box of the plan (npairs <= box_max x
-// (box_max + 2 VW) / VW), at most 4; boxes beyond 4 x kThreads pairs loop over
-// them from shared memory.
+// (box_max + 2 VW) / VW); boxes beyond that loop over the pairs from shared memory.
 template <typename T, int VW>
 void launch_k_forces_vw(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs,
                         cudaStream_t s) {
-    const int kp = forces_kp(p, VW);
-    const size_t sm = forces_smem(p, sizeof(T), VW, kp);
-    switch (kp) {
-        case 1: k_forces<T, VW, 1><<<blocks, kThreads, sm, s>>>(a, V, slabs, p.force_partials); break;
-        case 2: k_forces<T, VW, 2><<<blocks, kThreads, sm, s>>>(a, V, slabs, p.force_partials); break;
-        case 3: k_forces<T, VW, 3><<<blocks, kThreads, sm, s>>>(a, V, slabs, p.force_partials); break;
-        default: k_forces<T, VW, 4><<<blocks, kThreads, sm, s>>>(a, V, slabs, p.force_partials); break;
-    }
+    const ForceShape fs = forces_shape(p, VW);
+    const size_t sm = forces_smem(p, sizeof(T), VW, fs);
+    if constexpr (sizeof(T) == 4 && VW == 4)
+        if (fs.nt == 128) return launch_k_forces_nt<T, VW, 128>(p, a, V, blocks, slabs, fs.kp, sm, s);
+    launch_k_forces_nt<T, VW, kThreads>(p, a, V, blocks, slabs, fs.kp, sm, s);
 }
 
 // The widest aligned vector along c: VW must divide N3 and V must be VW-element aligned.
@@ -498,17 +526,20 @@ void launch_k_forces(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned b
         launch_k_forces_vw<T, 1>(p, a, V, blocks, slabs, s);
 }
 
-size_t forces_smem(const Plan& p, size_t real_size, int vw, int kp) {
+size_t forces_smem(const Plan& p, size_t real_size, int vw, ForceShape fs) {
     const int ld = p.box_max + 8;
-    const size_t ring = (size_t)kDepth * kp * kThreads * vw * real_size;
+    const size_t ring = (size_t)kDepth * fs.kp * fs.nt * vw * real_size;
     return (real_size == 4 ? ring_offset<float>(ld) : ring_offset<double>(ld)) * real_size + ring;
 }
 
-// Pairs per thread for the largest box of the plan, at most 4 (wider boxes loop over pairs).
-int forces_kp(const Plan& p, int vw) {
+// FP32 with 16-byte vectors: 128-thread CTAs with up to 6 pairs per thread when that holds
+// the box (fewer idle pair slots, the per-slice work spread over more pairs); otherwise 256
+// threads with at most 4 (wider boxes loop over the pairs).
+ForceShape forces_shape(const Plan& p, int vw) {
     const long long rows = std::min(p.box_max, p.n[1]);
     const long long npairs = rows * ((std::min(p.box_max, p.n[2]) + 3 * vw - 1) / vw);
-    return (int)std::min(4LL, (npairs + kThreads - 1) / kThreads);
+    if (p.real_size == 4 && vw == 4 && npairs <= 6 * 128) return {128, (int)std::max(1LL, (npairs + 127) / 128)};
+    return {kThreads, (int)std::max(1LL, std::min(4LL, (npairs + kThreads - 1) / kThreads))};
 }
 
 template <typename T>
@@ -529,21 +560,27 @@ cudaError_t forces_impl(const Plan& p, const double* pos, const double* q, int n
     return cudaGetLastError();
 }
 
-template <typename T, int VW>
+template <typename T, int VW, int NT>
 cudaError_t allow_forces_smem(int optin) {
-    cudaError_t e = allow_max_dynamic_smem(k_forces<T, VW, 1>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 2>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 3>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 4>, optin);
+    cudaError_t e = allow_max_dynamic_smem(k_forces<T, VW, 1, NT>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 2, NT>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 3, NT>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 4, NT>, optin);
+    if constexpr (NT == 128) {
+        if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 5, NT>, optin);
+        if (e == cudaSuccess) e = allow_max_dynamic_smem(k_forces<T, VW, 6, NT>, optin);
+    }
     return e;
 }
 
 template <typename T>
 cudaError_t configure_atoms(int optin) {
-    cudaError_t e = allow_forces_smem<T, 1>(optin);
-    if (e == cudaSuccess) e = allow_forces_smem<T, 2>(optin);
-    if constexpr (sizeof(T) == 4)
-        if (e == cudaSuccess) e = allow_forces_smem<T, 4>(optin);
+    cudaError_t e = allow_forces_smem<T, 1, kThreads>(optin);
+    if (e == cudaSuccess) e = allow_forces_smem<T, 2, kThreads>(optin);
+    if constexpr (sizeof(T) == 4) {
+        if (e == cudaSuccess) e = allow_forces_smem<T, 4, kThreads>(optin);
+        if (e == cudaSuccess) e = allow_forces_smem<T, 4, 128>(optin);
+    }
     return e;
 }
 
@@ -554,7 +591,7 @@ cudaError_t configure_atom_kernels(const Plan& p) {
     cudaError_t e = optin_smem(&optin);
     if (e != cudaSuccess) return e;
     for (int vw : {1, 2, 4})
-        if ((vw < 4 || p.real_size == 4) && forces_smem(p, p.real_size, vw, forces_kp(p, vw)) + 1024 > (size_t)optin)
+        if ((vw < 4 || p.real_size == 4) && forces_smem(p, p.real_size, vw, forces_shape(p, vw)) + 1024 > (size_t)optin)
             return cudaErrorInvalidConfiguration;
     return p.prec == HARTREE_FP64 ? configure_atoms<double>(optin) : configure_atoms<float>(optin);
 }

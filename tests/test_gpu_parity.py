@@ -199,15 +199,45 @@ def test_edge_single_charged_atom_unwrapped_positions(precision):
     assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
 
 
+@pytest.mark.parametrize("n3", [30, 32])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_edge_wide_cutoff_many_images(precision):
-    """Cutoff box wider than the cell: one grid point receives several images."""
-    S = synth.random_system((20, 24, 30), (3.0, 3.5, 4.0), 5, 0.6, seed=77, precision=precision)
+def test_edge_wide_cutoff_many_images(precision, n3):
+    """Cutoff box wider than the cell: one grid point receives several images (N3 = 32: the
+    FP32 gather on 16-byte vectors, N3 = 30: on 8-byte vectors)."""
+    S = synth.random_system((20, 24, n3), (3.0, 3.5, 4.0), 5, 0.6, seed=77, precision=precision)
     ref = O.solve_system(S)
     g = gpu_step(S, precision, cutoff_sigmas=8.0)
     tol = TOL[precision]
     assert rel_l2(g["vh"], ref["vh"]) <= tol["v"]
     assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_force_gathers_agree(precision):
+    """The force gather on 16-byte vectors (V_H 16-byte aligned; FP32: 128-thread CTAs) and on
+    8-byte vectors (V_H at an 8-byte offset) give the same forces up to summation order, and
+    both match the oracle."""
+    S, ref = oracle_cfg("cfg2")
+    plan = HartreePlan(S.n, S.cell, S.sigma, precision)
+    P, Q = dev(S.pos), dev(S.q)
+    vh, _ = plan.solve(P, Q)
+    off = 8 // vh.element_size()
+    buf = torch.empty(vh.numel() + off, dtype=vh.dtype, device="cuda")
+    vh8 = buf[off:].view(vh.shape)
+    vh8.copy_(vh)
+    assert vh.data_ptr() % 16 == 0 and vh8.data_ptr() % 16 == 8
+    f, phi = plan.forces(P, Q, vh)
+    f8, phi8 = plan.forces(P, Q, vh8)
+    torch.cuda.synchronize()
+    plan.device_status()
+    f, f8 = f.cpu().numpy(), f8.cpu().numpy()
+    scale = np.abs(ref["forces"]).max()
+    rel = {"fp64": 1e-13, "fp32": 1e-6}[precision]
+    assert np.max(np.abs(f - f8)) <= rel * scale
+    assert np.max(np.abs(phi.cpu().numpy() - phi8.cpu().numpy())) <= rel * np.abs(ref["phi"]).max()
+    for g in (f, f8):
+        assert np.max(np.abs(g - ref["forces"])) <= TOL[precision]["f"]
+    plan.close()
 
 
 def test_forces_recompute_when_vh_is_null():
