@@ -283,26 +283,61 @@ __device__ __forceinline__ void forces_weights(const AtomArgs<T>& a, const AtomP
     }
 }
 
+// The c groups of one atom's box along a grid row.  A group is VW consecutive elements
+// starting at a VW-aligned address; a row whose offset in V is r (mod VW) has aligned
+// starts at c = -r (mod VW).  The box covers c in [st, end1) and, when it wraps past N3,
+// also [0, l2).  Range 1 takes the groups from the aligned start at or below st, range 2
+// those from -r; an element counts only inside its own range, so nothing is counted twice
+// and the elements a group reads outside its range (the neighbouring rows' ends) get zero
+// weight.  With N2 N3 = 0 (mod VW) and V VW-aligned, every such read stays inside V.
+template <int VW>
+struct CGroups {
+    int st, end1, l2, n3;
+    __device__ __forceinline__ CGroups(int st_, int nw, int n3_)
+        : st(st_), end1(min(n3_, st_ + nw)), l2(max(0, st_ + nw - n3_)), n3(n3_) {}
+    __device__ __forceinline__ int cs0(int r) const { return st - (st + r) % VW; }
+    __device__ __forceinline__ int n1g(int r) const { return (end1 - cs0(r) + VW - 1) / VW; }
+    __device__ __forceinline__ int n2g(int r) const { return l2 > 0 ? (l2 + r + VW - 1) / VW : 0; }
+    // groups per row: the most over the residues rows can have
+    __device__ __forceinline__ int groups() const {
+        int step = n3 % VW == 0 ? VW : (n3 % 2 == 0 ? 2 : 1), g = 0;
+        for (int r = 0; r < VW; r += step) g = max(g, n1g(r) + n2g(r));
+        return g;
+    }
+    // first element (row-relative, may be negative) of group g of a row of residue r, and
+    // for each element the image-summed weight index t (-1: zero weight)
+    __device__ __forceinline__ int group(int r, int g, int* t) const {
+        const int m1 = n1g(r);
+        const bool second = g >= m1;
+        const int cs = second ? -r + VW * (g - m1) : cs0(r) + VW * g;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const int c = cs + e;
+            t[e] = second ? (c >= 0 && c < l2 ? c + n3 - st : -1) : (c >= st && c < end1 ? c - st : -1);
+        }
+        return g < m1 + n2g(r) ? cs : cs0(r);
+    }
+};
+
 // Force gather of one atom (or a slab of its a range) per CTA.
 //
 // V is periodic, so sum_m fac[m] V[(lo + m) mod n] = sum_t w[t] V[(lo + t) mod n]
 // over the min(cnt, n) distinct wrapped indices t, with the image-summed weight
 // w[t] = sum_{m = t (mod n), m < cnt} fac[m] (likewise for dfac).  Shared memory
-// holds these weights for the three axes; the c axis is laid out in slots of VW
-// starting at the VW-aligned wrapped index below the box, zero outside it, so
-// each (b row, c group) pair is one aligned vector load.  Per a slice a thread
-// contracts its KP pairs: r0 = sum_e V_e wc_e, r1 = sum_e V_e dwc_e, then
-// p0 += wb r0, py += dwb r0, pz += wb r1; slices are combined with wa / dwa in
-// compensated sums.  The gather is bound by loads in flight, not by
-// arithmetic: each thread keeps kDepth slices of its pairs in flight with
-// cp.async copies into a private ring in shared memory.
+// holds these weights for the three axes.  Each (b row, c group) pair is one
+// aligned vector load (CGroups), its VW c weights gathered into registers once.
+// Per a slice a thread contracts its KP pairs: r0 = sum_e V_e wc_e,
+// r1 = sum_e V_e dwc_e, then p0 += wb r0, py += dwb r0, pz += wb r1; slices are
+// combined with wa / dwa in compensated sums.  The gather is bound by loads in
+// flight, not by arithmetic: each thread keeps kDepth slices of its pairs in
+// flight with cp.async copies into a private ring in shared memory.
 template <typename T, int VW, int KP, int NT>
-__global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ? 4 : 3)) k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs,
-                                                     double* __restrict__ part) {
+__global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ? 4 : 3))
+    k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs, double* __restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int fb = a.fb;
     const int ld = fb + 8;
-    T* wf = reinterpret_cast<T*>(smem_raw);  // [3][ld] image-summed fac (c axis: per slot)
+    T* wf = reinterpret_cast<T*>(smem_raw);  // [3][ld] image-summed fac
     T* wd = wf + 3 * ld;                     // [3][ld] image-summed dfac
     __shared__ double red[4][NT / 32];
     const int atom = blockIdx.x / slabs, slab = blockIdx.x - atom * slabs;
@@ -311,20 +346,19 @@ __global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ?
     int nw[3], st[3];
     nw[0] = min(p.cnt[0], n1), nw[1] = min(p.cnt[1], n2), nw[2] = min(p.cnt[2], n3);
     st[0] = imod(p.lo[0], n1), st[1] = imod(p.lo[1], n2), st[2] = imod(p.lo[2], n3);
-    const int lead = st[2] % VW;  // VW divides n3
-    const int cst = st[2] - lead;
-    const int nslot = (lead + nw[2] + VW - 1) / VW * VW;
-    const int ng = nslot / VW;
-    forces_weights(a, p, atom, nw, lead, nslot, wf, wd, ld);
+    const CGroups<VW> cg(st[2], nw[2], n3);
+    const int ng = cg.groups();
+    forces_weights(a, p, atom, nw, 0, nw[2], wf, wd, ld);
     __syncthreads();
     const int ia0 = (int)((long long)nw[0] * slab / slabs), ia1 = (int)((long long)nw[0] * (slab + 1) / slabs);
     const long long slice = (long long)n2 * n3;
     const int npairs = nw[1] * ng;
+    const int rmul = n3 % VW;  // row residue: (b n3) mod VW = (b rmul) mod VW
     const T* wa = wf;
     const T* dwa = wd;
     T s0 = T(0), c0 = T(0), sx = T(0), cx = T(0), sy = T(0), cy = T(0), sz = T(0), cz = T(0);
     if (npairs <= NT * KP) {
-        int off[KP];  // b n3 + c of the pair's first point (< 2^24); pairs past the end read point 0 with zero weight
+        int off[KP];  // b n3 + c of the pair's first point; pairs past the end read row 0's first group with zero weight
         T wb[KP], dwb[KP], wc[KP][VW], dwc[KP][VW];
 #pragma unroll
         for (int u = 0; u < KP; ++u) {
@@ -333,15 +367,15 @@ __global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ?
             const int j = ok ? pr / ng : 0, g = ok ? pr - j * ng : 0;
             int bj = st[1] + j;
             if (bj >= n2) bj -= n2;
-            int cg = cst + g * VW;
-            if (cg >= n3) cg -= n3;
-            off[u] = ok ? bj * n3 + cg : 0;
+            int t[VW];
+            const int cs = cg.group(bj * rmul % VW, g, t);
+            off[u] = bj * n3 + cs;
             wb[u] = ok ? wf[ld + j] : T(0);
             dwb[u] = ok ? wd[ld + j] : T(0);
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                wc[u][e] = wf[2 * ld + g * VW + e];
-                dwc[u][e] = wd[2 * ld + g * VW + e];
+                wc[u][e] = t[e] >= 0 ? wf[2 * ld + t[e]] : T(0);
+                dwc[u][e] = t[e] >= 0 ? wd[2 * ld + t[e]] : T(0);
             }
         }
         // ring of kDepth slices of this thread's pairs in shared memory, filled by
@@ -392,7 +426,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ?
         }
         cp_async_wait<0>();
     } else {
-        // very wide boxes: pairs revisited per slice with weights from shared memory
+        // very wide boxes: pairs revisited per slice, their geometry recomputed
         for (int t = ia0; t < ia1; ++t) {
             int ai = st[0] + t;
             if (ai >= n1) ai -= n1;
@@ -402,15 +436,15 @@ __global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ?
                 const int j = pr / ng, g = pr - j * ng;
                 int bj = st[1] + j;
                 if (bj >= n2) bj -= n2;
-                int cg = cst + g * VW;
-                if (cg >= n3) cg -= n3;
+                int tc[VW];
+                const int cs = cg.group(bj * rmul % VW, g, tc);
                 T v[VW];
-                VecLoad<T, VW>::ld(Vs + bj * n3 + cg, v);
+                VecLoad<T, VW>::ld(Vs + bj * n3 + cs, v);
                 T r0 = T(0), r1 = T(0);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
-                    r0 += v[e] * wf[2 * ld + g * VW + e];
-                    r1 += v[e] * wd[2 * ld + g * VW + e];
+                    r0 += tc[e] >= 0 ? v[e] * wf[2 * ld + tc[e]] : T(0);
+                    r1 += tc[e] >= 0 ? v[e] * wd[2 * ld + tc[e]] : T(0);
                 }
                 p0 += wf[ld + j] * r0;
                 py += wd[ld + j] * r0;
@@ -510,17 +544,19 @@ void launch_k_forces_vw(const Plan& p, const AtomArgs<T>& a, const T* V, unsigne
     launch_k_forces_nt<T, VW, kThreads>(p, a, V, blocks, slabs, fs.kp, sm, s);
 }
 
-// The widest aligned vector along c: VW must divide N3 and V must be VW-element aligned.
+// The widest aligned vector along c: V must be VW-element aligned and VW must divide N2 N3
+// (every a slice then starts aligned; CGroups handles rows of any residue).
 template <typename T>
 void launch_k_forces(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs, cudaStream_t s) {
     const uintptr_t addr = reinterpret_cast<uintptr_t>(V);
+    const long long slice = (long long)p.n[1] * p.n[2];
     if constexpr (sizeof(T) == 4) {
-        if (p.n[2] % 4 == 0 && addr % 16 == 0) {
+        if (slice % 4 == 0 && addr % 16 == 0) {
             launch_k_forces_vw<T, 4>(p, a, V, blocks, slabs, s);
             return;
         }
     }
-    if (addr % (2 * sizeof(T)) == 0)
+    if (slice % 2 == 0 && addr % (2 * sizeof(T)) == 0)
         launch_k_forces_vw<T, 2>(p, a, V, blocks, slabs, s);
     else
         launch_k_forces_vw<T, 1>(p, a, V, blocks, slabs, s);
@@ -537,7 +573,8 @@ size_t forces_smem(const Plan& p, size_t real_size, int vw, ForceShape fs) {
 // threads with at most 4 (wider boxes loop over the pairs).
 ForceShape forces_shape(const Plan& p, int vw) {
     const long long rows = std::min(p.box_max, p.n[1]);
-    const long long npairs = rows * ((std::min(p.box_max, p.n[2]) + 3 * vw - 1) / vw);
+    // CGroups: at most (nw + 2 VW - 2) / VW + 2 groups per row, the wrapped range included
+    const long long npairs = rows * ((std::min(p.box_max, p.n[2]) + 2 * vw - 2) / vw + 2);
     if (p.real_size == 4 && vw == 4 && npairs <= 6 * 128) return {128, (int)std::max(1LL, (npairs + 127) / 128)};
     return {kThreads, (int)std::max(1LL, std::min(4LL, (npairs + kThreads - 1) / kThreads))};
 }

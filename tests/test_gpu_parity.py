@@ -240,6 +240,27 @@ def test_force_gathers_agree(precision):
     plan.close()
 
 
+@pytest.mark.parametrize("n", [(24, 18, 30), (20, 21, 30), (16, 20, 42)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_force_gather_row_residues(precision, n):
+    """Rows of V that start off the 16-byte grid (N3 = 2 mod 4): the gather reads aligned
+    groups that reach into the neighbouring rows with zero weight.  Atoms sit at the cell's
+    corners and faces, so their boxes wrap past N2 and N3."""
+    cell = (4.0, 4.5, 5.0)
+    rng = np.random.default_rng(sum(n))
+    L = np.asarray(cell)
+    corners = np.array([[0.02, 0.03, 0.01], [0.98, 0.97, 0.99], [0.5, 0.01, 0.99], [0.01, 0.99, 0.5]]) * L
+    pos = np.vstack([corners, rng.uniform(0.0, 1.0, size=(6, 3)) * L])
+    q = rng.uniform(-1.0, 1.0, size=pos.shape[0])
+    q -= q.mean()
+    S = synth.System("residues", n, cell, 0.45, pos, q, precision)
+    ref = O.solve_system(S, rc_sigmas=5.0)
+    g = gpu_step(S, precision, cutoff_sigmas=5.0)
+    tol = TOL[precision]
+    assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
+    assert np.max(np.abs(g["phi"] - ref["phi"])) <= tol["f"]
+
+
 def test_forces_recompute_when_vh_is_null():
     S, ref = oracle_cfg("cfg2")
     plan = HartreePlan(S.n, S.cell, S.sigma, "fp32")
