@@ -131,15 +131,18 @@ __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int
 // memory (a rank sort; indices in a list are distinct), so the summation order
 // is that of the leaf-selecting splat, then factors are staged in batches and
 // accumulated as there.  Longer lists take the leaf-selecting path.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 4) k_splat_binned(AtomArgs<T> a, T* __restrict__ rho, int tiles_b,
-                                                           int tiles_c, const int* __restrict__ cursor,
-                                                           const int4* __restrict__ list) {
+// Grid (tiles along c, b, a); FULL: every tile lies inside the grid (TA | N1, TB | N2, TC | N3).
+template <typename T, bool FULL>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 4)
+    k_splat_binned(AtomArgs<T> a, T* __restrict__ rho, const int* __restrict__ cursor,
+                   const int4* __restrict__ list) {
     __shared__ int4 ent[kBinCap];
     __shared__ int4 sorted[kBinCap];
     __shared__ __align__(16) T fa[kBatch][TA];
     __shared__ T fb[kBatch][TB], fc[kBatch][TC];
-    const int tile = blockIdx.x;
+    const int tiles_c = gridDim.x, tiles_b = gridDim.y;
+    const int tc = blockIdx.x, tb = blockIdx.y, ta = blockIdx.z;
+    const int tile = (ta * tiles_b + tb) * tiles_c + tc;
     const int L = cursor[tile];
     if (L > kBinCap) {
         splat_tile(a, rho, tiles_b, tiles_c, tile);
@@ -153,9 +156,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 4) k_splat_binn
         for (int f = 0; f < L; ++f) r += ent[f].x < v.x;
         sorted[r] = v;
     }
-    const int ta = tile / (tiles_b * tiles_c);
-    const int tb = (tile / tiles_c) % tiles_b;
-    const int tc = tile % tiles_c;
     const int a0 = ta * TA, b0 = tb * TB, c0 = tc * TC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T acc[TA];
@@ -168,25 +168,25 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 4) k_splat_binn
         for (int e = threadIdx.x; e < nb * TC; e += kThreads) {
             const int t = e / TC, k = e - t * TC;
             const int4 E = sorted[bb + t];
-            const T sc = c0 + k < a.n3 ? image_sum(a.fac + ((long long)E.x * 3 + 2) * a.fb, c0 + k, E.w & 0xffff,
-                                                   E.w >> 16, a.n3)
-                                       : T(0);
+            const T sc = FULL || c0 + k < a.n3 ? image_sum(a.fac + ((long long)E.x * 3 + 2) * a.fb, c0 + k,
+                                                           E.w & 0xffff, E.w >> 16, a.n3)
+                                               : T(0);
             const AtomPrep<T>& p = a.prep[E.x];
             fc[t][k] = p.qn * sc + p.ql * sc;
         }
         for (int e = threadIdx.x; e < nb * TA; e += kThreads) {
             const int t = e / TA, f = e - t * TA;
             const int4 E = sorted[bb + t];
-            fa[t][f] = a0 + f < a.n1
+            fa[t][f] = FULL || a0 + f < a.n1
                            ? image_sum(a.fac + (long long)E.x * 3 * a.fb, a0 + f, E.y & 0xffff, E.y >> 16, a.n1)
                            : T(0);
         }
         for (int e = threadIdx.x; e < nb * TB; e += kThreads) {
             const int t = e / TB, f = e - t * TB;
             const int4 E = sorted[bb + t];
-            fb[t][f] = b0 + f < a.n2 ? image_sum(a.fac + ((long long)E.x * 3 + 1) * a.fb, b0 + f, E.z & 0xffff,
-                                                 E.z >> 16, a.n2)
-                                     : T(0);
+            fb[t][f] = FULL || b0 + f < a.n2 ? image_sum(a.fac + ((long long)E.x * 3 + 1) * a.fb, b0 + f,
+                                                         E.z & 0xffff, E.z >> 16, a.n2)
+                                             : T(0);
         }
         __syncthreads();
         for (int t = 0; t < nb; ++t) {
@@ -196,12 +196,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 4) k_splat_binn
         }
     }
     const int b = b0 + warp, c = c0 + lane;
-    if (b < a.n2 && c < a.n3) {
+    const long long slice = (long long)a.n2 * a.n3;
+    T* out = rho + a0 * slice + (long long)b * a.n3 + c;
+    if (FULL) {
 #pragma unroll
-        for (int i = 0; i < TA; ++i) {
-            const int ia = a0 + i;
-            if (ia < a.n1) rho[((long long)ia * a.n2 + b) * a.n3 + c] = acc[i];
-        }
+        for (int i = 0; i < TA; ++i) out[i * slice] = acc[i];
+    } else if (b < a.n2 && c < a.n3) {
+#pragma unroll
+        for (int i = 0; i < TA; ++i)
+            if (a0 + i < a.n1) out[i * slice] = acc[i];
     }
 }
 
@@ -502,8 +505,11 @@ cudaError_t splat_impl(const Plan& p, const double* pos, const double* q, int n,
     cudaError_t e = prep_atoms<T>(p, a, true, s);
     if (e != cudaSuccess) return e;
     p.launches += 1;
-    k_splat_binned<T><<<(unsigned)p.n_tiles, kThreads, 0, s>>>(a, static_cast<T*>(rho), p.tiles[1], p.tiles[2],
-                                                                  p.bin_cursor, p.bin_list);
+    const dim3 grid((unsigned)p.tiles[2], (unsigned)p.tiles[1], (unsigned)p.tiles[0]);
+    if (p.n[0] % TA == 0 && p.n[1] % TB == 0 && p.n[2] % TC == 0)
+        k_splat_binned<T, true><<<grid, kThreads, 0, s>>>(a, static_cast<T*>(rho), p.bin_cursor, p.bin_list);
+    else
+        k_splat_binned<T, false><<<grid, kThreads, 0, s>>>(a, static_cast<T*>(rho), p.bin_cursor, p.bin_list);
     return cudaGetLastError();
 }
 
