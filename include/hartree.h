@@ -219,9 +219,13 @@ int hartree_plan_device_status(hartree_plan plan);
  * 2: the a pass) may have several compiled tile shapes (columns or lines per
  * CTA and threads per CTA); for FP32 b and a passes of 256 or 512 points
  * variants 2 and up are persistent kernels that stream tiles with TMA bulk
- * copies, those past the first with radix-32 stages.  hartree_plan_autotune
- * times every variant on the plan's own workspace (overwriting it; waits for
- * the stream; not capturable) and keeps the fastest; choice[3] (host, may be
+ * copies, those past the first with radix-32 stages.  The c passes have V
+ * variants each (plain tiles, then bulk-copy streams) and V * V picks: a pick
+ * v < V runs both c passes on variant v, a pick V + m runs the r2c pass on
+ * variant m / (V - 1) and the c2r pass on one of the other V - 1 variants.
+ * hartree_plan_autotune times every variant on the plan's own workspace
+ * (overwriting it; waits for the stream; not capturable) and keeps the
+ * fastest, the r2c and c2r passes each on its own; choice[3] (host, may be
  * NULL) receives the picks.  hartree_plan_set_variants applies picks saved
  * earlier (e.g. from a cache); out-of-range picks return HARTREE_ERR_INVALID.
  * Variants 0..2 apply the same operations to each element, so V_H is

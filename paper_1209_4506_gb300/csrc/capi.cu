@@ -451,8 +451,42 @@ int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    static const int passes[3][2] = {{0, 4}, {1, 3}, {2, 2}};
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    // time `reps` launches of pass `q` (twice: q and q2 when q2 >= 0) under the current variants
+    auto time_passes = [&](int q, int q2, float* ms) {
+        for (int rep = 0; rep < 3; ++rep) {  // warm-up
+            launch_poisson_pass(p, q, p.R, p.R, s);
+            if (q2 >= 0) launch_poisson_pass(p, q2, p.R, p.R, s);
+        }
+        cudaError_t r = cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 10; ++rep) {
+            launch_poisson_pass(p, q, p.R, p.R, s);
+            if (q2 >= 0) launch_poisson_pass(p, q2, p.R, p.R, s);
+        }
+        if (r == cudaSuccess) r = cudaEventRecord(e1, s);
+        if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(ms, e0, e1);
+        return r;
+    };
+    // c passes: each of r2c and c2r takes its own fastest variant
+    const int V = c_single_variants(p);
+    if (V > 1 && e == cudaSuccess) {
+        int best_v[2] = {0, 0};
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+            float best = 1e30f;
+            for (int v = 0; v < V && e == cudaSuccess; ++v) {
+                p.var[0] = v;
+                float ms = 0.f;
+                e = time_passes(q == 0 ? 0 : 4, -1, &ms);
+                if (e == cudaSuccess && ms < best) {
+                    best = ms;
+                    best_v[q] = v;
+                }
+            }
+        }
+        p.var[0] = c_variant_index(V, best_v[0], best_v[1]);
+    }
+    static const int passes[3][2] = {{0, 4}, {1, 3}, {2, -1}};
+    for (int k = 1; k < 3 && e == cudaSuccess; ++k) {
         if (k == 1 && p.prec == HARTREE_FP32_TC_SPLIT) continue;  // b passes run on the tensor cores
         const int nv = fast_variants(p, k);
         if (nv <= 1) continue;
@@ -460,15 +494,8 @@ int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice) {
         int best_v = 0;
         for (int v = 0; v < nv && e == cudaSuccess; ++v) {
             p.var[k] = v;
-            for (int rep = 0; rep < 3; ++rep)  // warm-up
-                for (int q = 0; q < 2; ++q) launch_poisson_pass(p, passes[k][q], p.R, p.R, s);
-            e = cudaEventRecord(e0, s);
-            for (int rep = 0; rep < 10; ++rep)
-                for (int q = 0; q < 2; ++q) launch_poisson_pass(p, passes[k][q], p.R, p.R, s);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            e = time_passes(passes[k][0], passes[k][1], &ms);
             if (e == cudaSuccess && ms < best) {
                 best = ms;
                 best_v = v;

@@ -1000,9 +1000,12 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
     FastArgs<T> a = make_fast_args<T>(p);
     long long grid = -1;
     if (pass == 0 || pass == 4) {
+        int vr = 0, vc = 0;
+        c_pass_variants(c_single_variants(p), p.var[0], &vr, &vc);
+        const int v = pass == 0 ? vr : vc;
         if constexpr (sizeof(T) == 4) {
             const void* grid_ptr = pass == 0 ? rho : vh;
-            const int sv = p.var[0] - line_variants(p.M);
+            const int sv = v - line_variants(p.M);
             if (sv >= 0 && line_stream_available(p) && reinterpret_cast<uintptr_t>(grid_ptr) % 16 == 0) {
                 with_line_stream_cfg(p.M, sv, [&](auto c) {
                     grid = c.launch(pass == 4, p.sm_count, rho, vh, a, p.d_err, s);
@@ -1010,7 +1013,7 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
                 return grid;
             }
         }
-        const int lv = p.var[0] < line_variants(p.M) ? p.var[0] : 0;  // misaligned grid: plain kernel
+        const int lv = v < line_variants(p.M) ? v : 0;  // misaligned grid: plain kernel
         with_line_cfg<T>(p.M, lv, [&](auto c) {
             grid = ((long long)p.n[0] * p.n[1] + c.lines - 1) / c.lines;
             c.launch(pass == 4, (unsigned)grid, rho, vh, a, s);
@@ -1048,9 +1051,30 @@ long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, c
                                   : launch_fast_pass_t<float>(p, pass, rho, vh, s);
 }
 
+int c_single_variants(const Plan& p) {
+    return (p.use_fast & 1) ? line_variants(p.M) + (line_stream_available(p) ? line_stream_variants(p.M) : 0) : 1;
+}
+
+void c_pass_variants(int V, int v, int* v_r2c, int* v_c2r) {
+    if (v < V || V < 2) {
+        *v_r2c = *v_c2r = v < V ? v : 0;
+        return;
+    }
+    const int m = v - V, r = m / (V - 1), c = m % (V - 1);
+    *v_r2c = r;
+    *v_c2r = c < r ? c : c + 1;
+}
+
+int c_variant_index(int V, int v_r2c, int v_c2r) {
+    if (v_r2c == v_c2r) return v_r2c;
+    return V + v_r2c * (V - 1) + (v_c2r < v_r2c ? v_c2r : v_c2r - 1);
+}
+
 int fast_variants(const Plan& p, int kind) {
-    if (kind == 0)
-        return (p.use_fast & 1) ? line_variants(p.M) + (line_stream_available(p) ? line_stream_variants(p.M) : 0) : 1;
+    if (kind == 0) {
+        const int V = c_single_variants(p);
+        return V * V;
+    }
     const int ax = kind == 1 ? 1 : 0;
     if (!(p.use_fast & (kind == 1 ? 2 : 4))) return 1;
     return col_variants(p.n[ax]) + (col_tma_available(p, ax) ? col_tma_variants(p.n[ax]) : 0);

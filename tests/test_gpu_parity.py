@@ -355,7 +355,7 @@ def test_kernel_variants_agree(shape, precision):
     v0 = v0.double()
     n_checked = 0
     for kind in range(3):
-        for var in range(16):
+        for var in range(64):
             choice = [0, 0, 0]
             choice[kind] = var
             try:
