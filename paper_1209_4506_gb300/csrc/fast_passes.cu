@@ -126,6 +126,71 @@ struct TwHi {
     __device__ __forceinline__ TwPair<T> operator[](int i) const { return TwPair<T>{p[i], mk(T(0), T(0))}; }
 };
 
+// Twiddles of one Stockham stage in the order the stage reads them.  A stage of radix R on
+// sub-transforms of NS points applies w^(k r N / (NS R)) to output r of butterfly k; its
+// table holds that factor at entry (r - 1) NS + k, so the lanes of a warp (consecutive k)
+// read consecutive entries, which shared memory serves without bank conflicts, instead of
+// entries k r apart in the transform's full table.  E: TwPair (compensated) or cpx (rounded).
+template <class E>
+struct StageTw {
+    const E* p;
+    int ns;
+};
+
+// The twiddle of output r of butterfly k; idx is its index in a full table.
+template <class Tw>
+__device__ __forceinline__ auto tw_fetch(const Tw& TW, int, int, int idx) {
+    return TW[idx];
+}
+template <typename T>
+__device__ __forceinline__ TwPair<T> tw_fetch(const StageTw<TwPair<T>>& TW, int k, int r, int) {
+    return TW.p[(r - 1) * TW.ns + k];
+}
+template <typename T>
+__device__ __forceinline__ TwPair<T> tw_fetch(const StageTw<cpx<T>>& TW, int k, int r, int) {
+    return TwPair<T>{TW.p[(r - 1) * TW.ns + k], mk(T(0), T(0))};
+}
+
+// Fill the StageTw table of stage (R, NS) of an N-point transform whose twiddle w^e is get(e TWS).
+template <int N, int R, int NS, int TWS, class E, class Get>
+__device__ __forceinline__ void fill_stage_tw(E* dst, const Get& get) {
+    for (int i = threadIdx.x; i < (R - 1) * NS; i += blockDim.x) {
+        const int r = i / NS + 1, k = i - (r - 1) * NS;
+        dst[i] = get((k * r * (N / (NS * R))) * TWS);
+    }
+}
+
+// Shared twiddle tables of the line (c) passes, radices R0 R1 R2 (R2 = 1: two stages): the
+// second and third stages' StageTw tables, then the r2c post-processing factors w_2M^k for
+// k <= M/2 (r2c) or the c2r pre-processing factors for k < M.
+template <int R0, int R1, int R2>
+struct LineTwLayout {
+    static constexpr int M = R0 * R1 * R2;
+    static constexpr int s2 = (R1 - 1) * R0;
+    static constexpr int s3 = R2 > 1 ? (R2 - 1) * R0 * R1 : 0;
+    static constexpr int fwd = s2 + s3 + M / 2 + 1;  // r2c entries (TwPair)
+    static constexpr int inv = s2 + s3 + M;          // c2r entries (cpx, rounded)
+};
+
+// Stage twiddle tables and the twiddles of the r2c post-processing (compensated pairs).
+template <typename T, int R0, int R1, int R2>
+__device__ __forceinline__ void fill_line_tw_fwd(TwPair<T>* tw, const TwPair<T>* g) {
+    using L = LineTwLayout<R0, R1, R2>;
+    auto get = [&](int e) { return g[e]; };
+    fill_stage_tw<L::M, R1, R0, 2>(tw, get);
+    if constexpr (R2 > 1) fill_stage_tw<L::M, R2, R0 * R1, 2>(tw + L::s2, get);
+    for (int k = threadIdx.x; k <= L::M / 2; k += blockDim.x) tw[L::s2 + L::s3 + k] = g[k];
+}
+// The same for the c2r pass (rounded values; its pre-processing reads k < M).
+template <typename T, int R0, int R1, int R2>
+__device__ __forceinline__ void fill_line_tw_inv(cpx<T>* tw, const TwPair<T>* g) {
+    using L = LineTwLayout<R0, R1, R2>;
+    auto get = [&](int e) { return g[e].h; };
+    fill_stage_tw<L::M, R1, R0, 2>(tw, get);
+    if constexpr (R2 > 1) fill_stage_tw<L::M, R2, R0 * R1, 2>(tw + L::s2, get);
+    for (int k = threadIdx.x; k < L::M; k += blockDim.x) tw[L::s2 + L::s3 + k] = g[k].h;
+}
+
 // One Stockham stage (radix R, sub-transform NS) for the BPT butterflies
 // j = j0 + t JSTEP of this thread; SYNC when src and dst share storage (or when
 // `hook` must run once every thread has read src: it runs after that barrier).
@@ -157,7 +222,8 @@ __device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, 
         const int k = j % NS;
         if constexpr (NS > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[t][r] = twmul<!INV>(v[t][r], TW[(k * r * (N / (NS * R))) * TWS], INV);
+            for (int r = 1; r < R; ++r)
+                v[t][r] = twmul<!INV>(v[t][r], tw_fetch(TW, k, r, (k * r * (N / (NS * R))) * TWS), INV);
         }
         dft<T, R, INV, !INV>(v[t]);
         const int o = (j - k) * R + k;
@@ -188,6 +254,28 @@ __device__ __forceinline__ void ftransform(const Src& src, const Sm& sm, const D
         fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, sm, col, j0, TW, NoPost{});
         __syncthreads();
         fstage<T, N, R2, R0 * R1, B2, JSTEP, TWS, INV, true>(sm, dst, col, j0, TW, post);
+    }
+}
+
+// ftransform for the line passes: the twiddles of the second and third stages come from
+// their StageTw tables at tw (LineTwLayout order); E is TwPair (forward) or cpx (inverse).
+template <typename T, int R0, int R1, int R2, int JSTEP, bool INV, bool FIRST_SYNC, class Src, class Sm, class Dst,
+          class E, class Hook = NoHook>
+__device__ __forceinline__ void line_ftransform(const Src& src, const Sm& sm, const Dst& dst, int j0, const E* tw,
+                                                const Hook& hook = Hook{}) {
+    constexpr int N = R0 * R1 * R2;
+    constexpr int B0 = (N / R0 + JSTEP - 1) / JSTEP, B1 = (N / R1 + JSTEP - 1) / JSTEP,
+                  B2 = (N / R2 + JSTEP - 1) / JSTEP;
+    const StageTw<E> tw2{tw, R0};
+    fstage<T, N, R0, 1, B0, JSTEP, 2, INV, FIRST_SYNC>(src, sm, 0, j0, tw2, NoPost{}, hook);  // no twiddles
+    __syncthreads();
+    if constexpr (R2 == 1) {
+        fstage<T, N, R1, R0, B1, JSTEP, 2, INV, true>(sm, dst, 0, j0, tw2, NoPost{});
+    } else {
+        fstage<T, N, R1, R0, B1, JSTEP, 2, INV, true>(sm, sm, 0, j0, tw2, NoPost{});
+        __syncthreads();
+        const StageTw<E> tw3{tw + LineTwLayout<R0, R1, R2>::s2, R0 * R1};
+        fstage<T, N, R2, R0 * R1, B2, JSTEP, 2, INV, true>(sm, dst, 0, j0, tw3, NoPost{});
     }
 }
 
@@ -444,15 +532,16 @@ __global__ void __launch_bounds__(NT, min_ctas<NT>()) k_r2c_fast(const T* __rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
     TwPair<T>* TW = reinterpret_cast<TwPair<T>*>(S + LINES * LDP);
-    for (int k = threadIdx.x; k < 2 * M; k += NT) TW[k] = a.twpc[k];
+    fill_line_tw_fwd<T, R0, R1, R2>(TW, a.twpc);
+    const TwPair<T>* TWP = TW + LineTwLayout<R0, R1, R2>::s2 + LineTwLayout<R0, R1, R2>::s3;  // w_2M^k, k <= M/2
     const int l = threadIdx.x / TPL, j0 = threadIdx.x % TPL;
     const long long gline = (long long)blockIdx.x * LINES + l;
     const bool act = gline < (long long)a.n1 * a.n2;
     LineRealIn<T> src{reinterpret_cast<const cpx<T>*>(rho + (act ? gline : 0) * a.n3), act};
     LineSmem<T> sm{S + l * LDP};
     __syncthreads();
-    // M-point transform of z (twiddles exp(-2 pi i e / M) = table entry 2e)
-    ftransform<T, R0, R1, R2, TPL, 2, false, false>(src, sm, sm, 0, j0, TW, NoPost{});
+    // M-point transform of z (twiddles exp(-2 pi i e / M) = entry 2e of the 2M-point table)
+    line_ftransform<T, R0, R1, R2, TPL, false, false>(src, sm, sm, j0, TW);
     __syncthreads();
     // X[k] = E[k] + w^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M;
     // the pair k, M - k shares its loads: E[M-k] = conj E[k], O[M-k] = conj O[k], w^(M-k) = -conj w^k,
@@ -466,7 +555,7 @@ __global__ void __launch_bounds__(NT, min_ctas<NT>()) k_r2c_fast(const T* __rest
             const cpx<T> E = scale(z1 + z2, half);
             const cpx<T> d = z1 - z2;
             const cpx<T> O = mk(d.im * half, -d.re * half);
-            const cpx<T> t = twmul(O, TW[k], false);
+            const cpx<T> t = twmul(O, TWP[k], false);
             out[k] = E + t;
             out[M - k] = conjg(E - t);
         }
@@ -480,17 +569,18 @@ __global__ void __launch_bounds__(NT, min_ctas<NT>()) k_c2r_fast(T* __restrict__
     constexpr int LDP = M + M / 16 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
-    TwPair<T>* TW = reinterpret_cast<TwPair<T>*>(S + LINES * LDP);
-    for (int k = threadIdx.x; k < 2 * M; k += NT) TW[k] = a.twpc[k];
+    cpx<T>* TW = S + LINES * LDP;
+    fill_line_tw_inv<T, R0, R1, R2>(TW, a.twpc);
+    const TwHi<T> TWQ{TW + LineTwLayout<R0, R1, R2>::s2 + LineTwLayout<R0, R1, R2>::s3};  // k < M
     const int l = threadIdx.x / TPL, j0 = threadIdx.x % TPL;
     const long long gline = (long long)blockIdx.x * LINES + l;
     const bool act = gline < (long long)a.n1 * a.n2;
     const long long gl = act ? gline : 0;
     LineSmem<T> sm{S + l * LDP};
     __syncthreads();
-    LineC2RIn<T> src{a.W + gl * a.ldc, TW, M, act};
+    LineC2RIn<T, TwHi<T>> src{a.W + gl * a.ldc, TWQ, M, act};
     LineRealOut<T> dst{reinterpret_cast<cpx<T>*>(vout + gl * a.n3), act};
-    ftransform<T, R0, R1, R2, TPL, 2, true, false>(src, sm, dst, 0, j0, TW, NoPost{});
+    line_ftransform<T, R0, R1, R2, TPL, true, false>(src, sm, dst, j0, static_cast<const cpx<T>*>(TW));
 }
 
 // ------------------------------------------------------------------ bulk-streamed c passes (FP32)
@@ -519,17 +609,16 @@ template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_r2c_stream(const float* __restrict__ rho, FastArgs<float> a, int ntiles, int* err) {
     constexpr int M = R0 * R1 * R2;
-    constexpr int N = M;
     constexpr int TPL = NT / LINES;
     constexpr int LDP = M + M / 16 + 1;
     constexpr int SLOT = LINES * M;  // complex elements per ring slot
-    constexpr int B0 = (N / R0 + TPL - 1) / TPL, B1 = (N / R1 + TPL - 1) / TPL, B2 = (N / R2 + TPL - 1) / TPL;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<float>* ring = reinterpret_cast<cpx<float>*>(smem_raw);
     cpx<float>* S = ring + NBUF * SLOT;
     TwPair<float>* TW = reinterpret_cast<TwPair<float>*>(S + LINES * LDP);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(TW + 2 * M);
-    for (int k = threadIdx.x; k < 2 * M; k += NT) TW[k] = a.twpc[k];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(TW + LineTwLayout<R0, R1, R2>::fwd);
+    fill_line_tw_fwd<float, R0, R1, R2>(TW, a.twpc);
+    const TwPair<float>* TWP = TW + LineTwLayout<R0, R1, R2>::s2 + LineTwLayout<R0, R1, R2>::s3;
     const long long nlines = (long long)a.n1 * a.n2;
     auto issue = [&](int t, int b) {
         const long long l0 = (long long)t * LINES;
@@ -566,16 +655,9 @@ __global__ void __launch_bounds__(NT, MINB)
             const int tn = t + NBUF * gridDim.x;
             if (threadIdx.x == 0 && tn < ntiles) issue(tn, b);
         };
-        // M-point transform of z (twiddles exp(-2 pi i e / M) = table entry 2e)
-        fstage<float, N, R0, 1, B0, TPL, 2, false, true>(src, sm, 0, j0, TW, NoPost{}, refill);
-        __syncthreads();
-        if constexpr (R2 == 1) {
-            fstage<float, N, R1, R0, B1, TPL, 2, false, true>(sm, sm, 0, j0, TW, NoPost{});
-        } else {
-            fstage<float, N, R1, R0, B1, TPL, 2, false, true>(sm, sm, 0, j0, TW, NoPost{});
-            __syncthreads();
-            fstage<float, N, R2, R0 * R1, B2, TPL, 2, false, true>(sm, sm, 0, j0, TW, NoPost{});
-        }
+        // M-point transform of z (twiddles exp(-2 pi i e / M) = entry 2e of the 2M-point table)
+        line_ftransform<float, R0, R1, R2, TPL, false, true>(src, sm, sm, j0, static_cast<const TwPair<float>*>(TW),
+                                                               refill);
         __syncthreads();
         // X[k] and X[M - k] from one pair of loads, as in k_r2c_fast
         if (act) {
@@ -586,7 +668,7 @@ __global__ void __launch_bounds__(NT, MINB)
                 const cpx<float> E = scale(z1 + z2, 0.5f);
                 const cpx<float> d = z1 - z2;
                 const cpx<float> O = mk(d.im * 0.5f, -d.re * 0.5f);
-                const cpx<float> t = twmul(O, TW[kk], false);
+                const cpx<float> t = twmul(O, TWP[kk], false);
                 out[kk] = E + t;
                 out[M - kk] = conjg(E - t);
             }
@@ -598,18 +680,16 @@ template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_c2r_stream(float* __restrict__ vout, FastArgs<float> a, int ntiles, int* err) {
     constexpr int M = R0 * R1 * R2;
-    constexpr int N = M;
     constexpr int TPL = NT / LINES;
     constexpr int LDP = M + M / 16 + 1;
-    constexpr int B0 = (N / R0 + TPL - 1) / TPL, B1 = (N / R1 + TPL - 1) / TPL, B2 = (N / R2 + TPL - 1) / TPL;
     const int slot = LINES * a.ldc;  // complex elements per ring slot: LINES padded rows
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<float>* ring = reinterpret_cast<cpx<float>*>(smem_raw);
     cpx<float>* S = ring + NBUF * slot;
     cpx<float>* TWh = S + LINES * LDP;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(TWh + 2 * M);
-    for (int k = threadIdx.x; k < 2 * M; k += NT) TWh[k] = a.twpc[k].h;
-    const TwHi<float> TW{TWh};
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(TWh + LineTwLayout<R0, R1, R2>::inv);
+    fill_line_tw_inv<float, R0, R1, R2>(TWh, a.twpc);
+    const TwHi<float> TWQ{TWh + LineTwLayout<R0, R1, R2>::s2 + LineTwLayout<R0, R1, R2>::s3};
     const long long nlines = (long long)a.n1 * a.n2;
     auto issue = [&](int t, int b) {
         const long long l0 = (long long)t * LINES;
@@ -641,21 +721,14 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         const long long gline = (long long)t * LINES + l;
         const bool act = gline < nlines;
-        LineC2RIn<float, TwHi<float>> src{ring + b * slot + l * a.ldc, TW, M, act};
+        LineC2RIn<float, TwHi<float>> src{ring + b * slot + l * a.ldc, TWQ, M, act};
         LineRealOut<float> dst{reinterpret_cast<cpx<float>*>(vout + (act ? gline : 0) * a.n3), act};
         auto refill = [&] {
             const int tn = t + NBUF * gridDim.x;
             if (threadIdx.x == 0 && tn < ntiles) issue(tn, b);
         };
-        fstage<float, N, R0, 1, B0, TPL, 2, true, true>(src, sm, 0, j0, TW, NoPost{}, refill);
-        __syncthreads();
-        if constexpr (R2 == 1) {
-            fstage<float, N, R1, R0, B1, TPL, 2, true, true>(sm, dst, 0, j0, TW, NoPost{});
-        } else {
-            fstage<float, N, R1, R0, B1, TPL, 2, true, true>(sm, sm, 0, j0, TW, NoPost{});
-            __syncthreads();
-            fstage<float, N, R2, R0 * R1, B2, TPL, 2, true, true>(sm, dst, 0, j0, TW, NoPost{});
-        }
+        line_ftransform<float, R0, R1, R2, TPL, true, true>(src, sm, dst, j0, static_cast<const cpx<float>*>(TWh),
+                                                             refill);
     }
 }
 
@@ -681,7 +754,9 @@ template <typename T, int LINES, int NT, int R0, int R1, int R2>
 struct LineCfg {
     static constexpr int lines = LINES, m = R0 * R1 * R2;
     static size_t smem() {
-        return (size_t)LINES * (m + m / 16 + 1) * sizeof(cpx<T>) + (size_t)2 * m * sizeof(TwPair<T>);
+        const size_t tw = std::max((size_t)LineTwLayout<R0, R1, R2>::fwd * sizeof(TwPair<T>),
+                                   (size_t)LineTwLayout<R0, R1, R2>::inv * sizeof(cpx<T>));
+        return (size_t)LINES * (m + m / 16 + 1) * sizeof(cpx<T>) + tw;
     }
     static cudaError_t configure(int optin) {
         cudaError_t e;
@@ -704,10 +779,12 @@ struct LineStreamCfg {
     static constexpr int lines = LINES, m = R0 * R1 * R2;
     static size_t smem_work() { return (size_t)LINES * (m + m / 16 + 1) * sizeof(cpx<float>) + NBUF * 8; }
     static size_t smem_r2c() {
-        return (size_t)NBUF * LINES * m * sizeof(cpx<float>) + smem_work() + (size_t)2 * m * sizeof(TwPair<float>);
+        return (size_t)NBUF * LINES * m * sizeof(cpx<float>) + smem_work() +
+               (size_t)LineTwLayout<R0, R1, R2>::fwd * sizeof(TwPair<float>);
     }
     static size_t smem_c2r(int ldc) {
-        return (size_t)NBUF * LINES * ldc * sizeof(cpx<float>) + smem_work() + (size_t)2 * m * sizeof(cpx<float>);
+        return (size_t)NBUF * LINES * ldc * sizeof(cpx<float>) + smem_work() +
+               (size_t)LineTwLayout<R0, R1, R2>::inv * sizeof(cpx<float>);
     }
     static size_t smem() { return 0; }  // checked per kernel in configure()
     static cudaError_t configure(int optin) {
