@@ -131,24 +131,28 @@ struct TwHi {
 // table holds that factor at entry (r - 1) NS + k, so the lanes of a warp (consecutive k)
 // read consecutive entries, which shared memory serves without bank conflicts, instead of
 // entries k r apart in the transform's full table.  E: TwPair (compensated) or cpx (rounded).
-template <class E>
+template <class E, int NS>
 struct StageTw {
     const E* p;
-    int ns;
 };
+
+template <class Tw>
+struct is_stage_tw : std::false_type {};
+template <class E, int NS>
+struct is_stage_tw<StageTw<E, NS>> : std::true_type {};
 
 // The twiddle of output r of butterfly k; idx is its index in a full table.
 template <class Tw>
-__device__ __forceinline__ auto tw_fetch(const Tw& TW, int, int, int idx) {
+__device__ __forceinline__ decltype(auto) tw_fetch(const Tw& TW, int, int, int idx) {
     return TW[idx];
 }
-template <typename T>
-__device__ __forceinline__ TwPair<T> tw_fetch(const StageTw<TwPair<T>>& TW, int k, int r, int) {
-    return TW.p[(r - 1) * TW.ns + k];
+template <typename T, int NS>
+__device__ __forceinline__ TwPair<T> tw_fetch(const StageTw<TwPair<T>, NS>& TW, int k, int r, int) {
+    return TW.p[(r - 1) * NS + k];
 }
-template <typename T>
-__device__ __forceinline__ TwPair<T> tw_fetch(const StageTw<cpx<T>>& TW, int k, int r, int) {
-    return TwPair<T>{TW.p[(r - 1) * TW.ns + k], mk(T(0), T(0))};
+template <typename T, int NS>
+__device__ __forceinline__ TwPair<T> tw_fetch(const StageTw<cpx<T>, NS>& TW, int k, int r, int) {
+    return TwPair<T>{TW.p[(r - 1) * NS + k], mk(T(0), T(0))};
 }
 
 // Fill the StageTw table of stage (R, NS) of an N-point transform whose twiddle w^e is get(e TWS).
@@ -191,6 +195,38 @@ __device__ __forceinline__ void fill_line_tw_inv(cpx<T>* tw, const TwPair<T>* g)
     for (int k = threadIdx.x; k < L::M; k += blockDim.x) tw[L::s2 + L::s3 + k] = g[k].h;
 }
 
+// Shared twiddle tables of the column (b, a) passes, radices R0 R1 R2 (R2 = 1: two stages):
+// the StageTw tables of the forward (or MODE 1 inverse) stages 2 and 3, then for MODE 2 those
+// of the inverse transform, whose radices run in the reverse order (R2 R1 R0); an inverse
+// table equal to a forward one (R0 = R2, or R0 = R1 for two stages) is shared.
+template <int R0, int R1, int R2, int MODE>
+struct ColTwLayout {
+    static constexpr int N = R0 * R1 * R2;
+    static constexpr int f2 = 0, f3 = (R1 - 1) * R0;  // T(R1, NS = R0), T(R2, NS = R0 R1)
+    static constexpr int fend = f3 + (R2 > 1 ? (R2 - 1) * R0 * R1 : 0);
+    static constexpr bool share = MODE != 2 || (R2 > 1 ? R0 == R2 : R0 == R1);
+    // MODE 2 inverse: R2 > 1: T(R1, NS = R2) at i2, T(R0, NS = R2 R1) at i3; R2 = 1: T(R0, NS = R1) at i2
+    static constexpr int i2 = share ? f2 : fend;
+    static constexpr int i3 = share ? f3 : fend + (R1 - 1) * R2;
+    static constexpr int total = share ? fend : (R2 > 1 ? i3 + (R0 - 1) * R2 * R1 : fend + (R0 - 1) * R1);
+};
+
+template <typename T, int R0, int R1, int R2, int MODE>
+__device__ __forceinline__ void fill_col_tw(TwPair<T>* tw, const TwPair<T>* g) {
+    using L = ColTwLayout<R0, R1, R2, MODE>;
+    auto get = [&](int e) { return g[e]; };
+    fill_stage_tw<L::N, R1, R0, 1>(tw + L::f2, get);
+    if constexpr (R2 > 1) fill_stage_tw<L::N, R2, R0 * R1, 1>(tw + L::f3, get);
+    if constexpr (!L::share) {
+        if constexpr (R2 > 1) {
+            fill_stage_tw<L::N, R1, R2, 1>(tw + L::i2, get);
+            fill_stage_tw<L::N, R0, R2 * R1, 1>(tw + L::i3, get);
+        } else {
+            fill_stage_tw<L::N, R0, R1, 1>(tw + L::i2, get);
+        }
+    }
+}
+
 // One Stockham stage (radix R, sub-transform NS) for the BPT butterflies
 // j = j0 + t JSTEP of this thread; SYNC when src and dst share storage (or when
 // `hook` must run once every thread has read src: it runs after that barrier).
@@ -222,8 +258,12 @@ __device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, 
         const int k = j % NS;
         if constexpr (NS > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r)
-                v[t][r] = twmul<!INV>(v[t][r], tw_fetch(TW, k, r, (k * r * (N / (NS * R))) * TWS), INV);
+            for (int r = 1; r < R; ++r) {
+                if constexpr (is_stage_tw<Tw>::value)
+                    v[t][r] = twmul<!INV>(v[t][r], tw_fetch(TW, k, r, 0), INV);
+                else
+                    v[t][r] = twmul<!INV>(v[t][r], TW[(k * r * (N / (NS * R))) * TWS], INV);
+            }
         }
         dft<T, R, INV, !INV>(v[t]);
         const int o = (j - k) * R + k;
@@ -235,26 +275,33 @@ __device__ __forceinline__ void fstage(const Src& src, const Dst& dst, int col, 
     }
 }
 
-// Whole transform of a tile: stage 0 from src, the rest in place in `sm`,
-// the last stage through `post` into dst.  Threads: col, j0 in [0, JSTEP).
-template <typename T, int R0, int R1, int R2, int JSTEP, int TWS, bool INV, bool FIRST_SYNC, class Src, class Sm,
-          class Dst, class Post, class Tw, class Hook = NoHook>
+// Whole transform of a column tile: stage 0 from src, the rest in place in `sm`, the last
+// stage into dst, twiddles w^e at tw[e] (a full table).  Threads: col, j0 in [0, JSTEP).
+template <typename T, int R0, int R1, int R2, int JSTEP, bool INV, bool FIRST_SYNC, class Src, class Sm, class Dst>
 __device__ __forceinline__ void ftransform(const Src& src, const Sm& sm, const Dst& dst, int col, int j0,
-                                           const Tw& TW, const Post& post, const Hook& hook = Hook{}) {
+                                           const TwPair<T>* tw) {
     constexpr int N = R0 * R1 * R2;
     constexpr int B0 = (N / R0 + JSTEP - 1) / JSTEP, B1 = (N / R1 + JSTEP - 1) / JSTEP,
                   B2 = (N / R2 + JSTEP - 1) / JSTEP;
+    fstage<T, N, R0, 1, B0, JSTEP, 1, INV, FIRST_SYNC>(src, sm, col, j0, tw, NoPost{});
+    __syncthreads();
     if constexpr (R2 == 1) {
-        fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{}, hook);
-        __syncthreads();
-        fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, dst, col, j0, TW, post);
+        fstage<T, N, R1, R0, B1, JSTEP, 1, INV, true>(sm, dst, col, j0, tw, NoPost{});
     } else {
-        fstage<T, N, R0, 1, B0, JSTEP, TWS, INV, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{}, hook);
+        fstage<T, N, R1, R0, B1, JSTEP, 1, INV, true>(sm, sm, col, j0, tw, NoPost{});
         __syncthreads();
-        fstage<T, N, R1, R0, B1, JSTEP, TWS, INV, true>(sm, sm, col, j0, TW, NoPost{});
-        __syncthreads();
-        fstage<T, N, R2, R0 * R1, B2, JSTEP, TWS, INV, true>(sm, dst, col, j0, TW, post);
+        fstage<T, N, R2, R0 * R1, B2, JSTEP, 1, INV, true>(sm, dst, col, j0, tw, NoPost{});
     }
+}
+
+// The twiddles of one stage of a column transform: with STAGE, its StageTw table at tw + off
+// (ColTwLayout); else the full table tw.
+template <bool STAGE, int NS, class E>
+__device__ __forceinline__ auto stage_tw(const E* tw, int off) {
+    if constexpr (STAGE)
+        return StageTw<E, NS>{tw + off};
+    else
+        return tw;
 }
 
 // ftransform for the line passes: the twiddles of the second and third stages come from
@@ -266,7 +313,7 @@ __device__ __forceinline__ void line_ftransform(const Src& src, const Sm& sm, co
     constexpr int N = R0 * R1 * R2;
     constexpr int B0 = (N / R0 + JSTEP - 1) / JSTEP, B1 = (N / R1 + JSTEP - 1) / JSTEP,
                   B2 = (N / R2 + JSTEP - 1) / JSTEP;
-    const StageTw<E> tw2{tw, R0};
+    const StageTw<E, R0> tw2{tw};
     fstage<T, N, R0, 1, B0, JSTEP, 2, INV, FIRST_SYNC>(src, sm, 0, j0, tw2, NoPost{}, hook);  // no twiddles
     __syncthreads();
     if constexpr (R2 == 1) {
@@ -274,7 +321,7 @@ __device__ __forceinline__ void line_ftransform(const Src& src, const Sm& sm, co
     } else {
         fstage<T, N, R1, R0, B1, JSTEP, 2, INV, true>(sm, sm, 0, j0, tw2, NoPost{});
         __syncthreads();
-        const StageTw<E> tw3{tw + LineTwLayout<R0, R1, R2>::s2, R0 * R1};
+        const StageTw<E, R0 * R1> tw3{tw + LineTwLayout<R0, R1, R2>::s2};
         fstage<T, N, R2, R0 * R1, B2, JSTEP, 2, INV, true>(sm, dst, 0, j0, tw3, NoPost{});
     }
 }
@@ -304,7 +351,7 @@ __device__ __forceinline__ void fstage_green_pivot(const Sm& sm, int col, int j0
         if (GUARD && j >= NS) continue;
         if constexpr (NS > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[t][r] = twmul<true>(v[t][r], TW[j * r], false);
+            for (int r = 1; r < R; ++r) v[t][r] = twmul<true>(v[t][r], tw_fetch(TW, j, r, j * r), false);
         }
         dft<T, R, false, true>(v[t]);
 #pragma unroll
@@ -317,27 +364,31 @@ __device__ __forceinline__ void fstage_green_pivot(const Sm& sm, int col, int j0
 
 // Forward transform of a tile (stage 0 from src), `green` on the spectrum, and
 // the inverse transform (radices reversed; last stage into dst), in place in sm.
-template <typename T, int R0, int R1, int R2, int JSTEP, bool FIRST_SYNC, class Src, class Sm, class Dst, class Tw,
-          class Green>
+// STAGE: twiddles from the ColTwLayout<R0, R1, R2, 2> tables at tw, else from the full table tw.
+template <typename T, int R0, int R1, int R2, int JSTEP, bool FIRST_SYNC, bool STAGE, class Src, class Sm,
+          class Dst, class Green>
 __device__ __forceinline__ void ftransform_green(const Src& src, const Sm& sm, const Dst& dst, int col, int j0,
-                                                 const Tw& TW, const Green& green) {
+                                                 const TwPair<T>* tw, const Green& green) {
+    using L = ColTwLayout<R0, R1, R2, 2>;
     constexpr int N = R0 * R1 * R2;
     constexpr int B0 = (N / R0 + JSTEP - 1) / JSTEP, B1 = (N / R1 + JSTEP - 1) / JSTEP,
                   B2 = (N / R2 + JSTEP - 1) / JSTEP;
-    fstage<T, N, R0, 1, B0, JSTEP, 1, false, FIRST_SYNC>(src, sm, col, j0, TW, NoPost{});
+    const auto tw2 = stage_tw<STAGE, R0>(tw, L::f2);
+    fstage<T, N, R0, 1, B0, JSTEP, 1, false, FIRST_SYNC>(src, sm, col, j0, tw2, NoPost{});  // no twiddles
     __syncthreads();
     if constexpr (R2 == 1) {
-        fstage_green_pivot<T, N, R1, B1, JSTEP>(sm, col, j0, TW, green);
+        fstage_green_pivot<T, N, R1, B1, JSTEP>(sm, col, j0, tw2, green);
         __syncthreads();
-        fstage<T, N, R0, R1, B0, JSTEP, 1, true, true>(sm, dst, col, j0, TW, NoPost{});
+        fstage<T, N, R0, R1, B0, JSTEP, 1, true, true>(sm, dst, col, j0, stage_tw<STAGE, R1>(tw, L::i2), NoPost{});
     } else {
-        fstage<T, N, R1, R0, B1, JSTEP, 1, false, true>(sm, sm, col, j0, TW, NoPost{});
+        fstage<T, N, R1, R0, B1, JSTEP, 1, false, true>(sm, sm, col, j0, tw2, NoPost{});
         __syncthreads();
-        fstage_green_pivot<T, N, R2, B2, JSTEP>(sm, col, j0, TW, green);
+        fstage_green_pivot<T, N, R2, B2, JSTEP>(sm, col, j0, stage_tw<STAGE, R0 * R1>(tw, L::f3), green);
         __syncthreads();
-        fstage<T, N, R1, R2, B1, JSTEP, 1, true, true>(sm, sm, col, j0, TW, NoPost{});
+        fstage<T, N, R1, R2, B1, JSTEP, 1, true, true>(sm, sm, col, j0, stage_tw<STAGE, R2>(tw, L::i2), NoPost{});
         __syncthreads();
-        fstage<T, N, R0, R2 * R1, B0, JSTEP, 1, true, true>(sm, dst, col, j0, TW, NoPost{});
+        fstage<T, N, R0, R2 * R1, B0, JSTEP, 1, true, true>(sm, dst, col, j0, stage_tw<STAGE, R2 * R1>(tw, L::i3),
+                                                           NoPost{});
     }
 }
 
@@ -371,7 +422,7 @@ __global__ void __launch_bounds__(NT, MODE == 2 && min_ctas<NT>() > 2 ? min_ctas
     const int col = threadIdx.x % COLS, j0 = threadIdx.x / COLS;
     __syncthreads();
     if constexpr (MODE != 2) {
-        ftransform<T, R0, R1, R2, JSTEP, 1, MODE == 1, false>(g, sm, g, col, j0, TW, NoPost{});
+        ftransform<T, R0, R1, R2, JSTEP, MODE == 1, false>(g, sm, g, col, j0, static_cast<const TwPair<T>*>(TW));
     } else {
         // forward, then 4 pi / |G|^2 / N and the E_H partial on the last stage's outputs
         const cpx<T> gb = a.gsqb[line];
@@ -391,7 +442,8 @@ __global__ void __launch_bounds__(NT, MODE == 2 && min_ctas<NT>() > 2 ? min_ctas
             }
             v = scale(v, inv * a.green_scale);
         };
-        ftransform_green<T, R0, R1, R2, JSTEP, false>(g, sm, g, col, j0, TW, green);
+        ftransform_green<T, R0, R1, R2, JSTEP, false, false>(g, sm, g, col, j0, static_cast<const TwPair<T>*>(TW),
+                                                             green);
         const double bs = block_sum_comp(sum, -comp, red);
         if (threadIdx.x == 0) a.eh_partials[blockIdx.x] = bs;
     }
@@ -429,10 +481,13 @@ __global__ void __launch_bounds__(NT, MINB)
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     cpx<float>* bufs = reinterpret_cast<cpx<float>*>(base);
     TwPair<float>* TW = reinterpret_cast<TwPair<float>*>(bufs + NBUF * N * COLS);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(TW + N);
+    // the a pass (MODE 2) reads its twiddles from stage-ordered tables, the b passes from the full table
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(TW + (MODE == 2 ? ColTwLayout<R0, R1, R2, 2>::total : N));
     double* red = reinterpret_cast<double*>(mbar + NBUF);  // one double per warp
-    const TwPair<float>* twg = MODE == 2 ? a.twpa : a.twpb;
-    for (int k = threadIdx.x; k < N; k += NT) TW[k] = twg[k];
+    if constexpr (MODE == 2)
+        fill_col_tw<float, R0, R1, R2, 2>(TW, a.twpa);
+    else
+        for (int k = threadIdx.x; k < N; k += NT) TW[k] = a.twpb[k];
     if (threadIdx.x == 0) {
         for (int b = 0; b < NBUF; ++b) mbar_init(&mbar[b], 1);
         fence_barrier_init();
@@ -479,7 +534,8 @@ __global__ void __launch_bounds__(NT, MINB)
         parity ^= 1u << b;
         ColSmem<float, COLS> sm{bufs + b * N * COLS};
         if constexpr (MODE != 2) {
-            ftransform<float, R0, R1, R2, JSTEP, 1, MODE == 1, true>(sm, sm, sm, col, j0, TW, NoPost{});
+            ftransform<float, R0, R1, R2, JSTEP, MODE == 1, true>(sm, sm, sm, col, j0,
+                                                                  static_cast<const TwPair<float>*>(TW));
         } else {
             const int line = t / chunks, c0 = (t - line * chunks) * COLS;
             const int nc = min(COLS, a.nh - c0);
@@ -497,7 +553,8 @@ __global__ void __launch_bounds__(NT, MINB)
                 tile_sum = fmaf(v.re * v.re + v.im * v.im, inv, tile_sum);
                 v = scale(v, inv * a.green_scale);
             };
-            ftransform_green<float, R0, R1, R2, JSTEP, true>(sm, sm, sm, col, j0, TW, green);
+            ftransform_green<float, R0, R1, R2, JSTEP, true, true>(sm, sm, sm, col, j0,
+                                                                   static_cast<const TwPair<float>*>(TW), green);
             if (col < nc) {  // compensated across tiles
                 const float term = mult * tile_sum - comp;
                 const float tt = sum + term;
@@ -736,7 +793,7 @@ __global__ void __launch_bounds__(NT, MINB)
 template <typename T, int COLS, int NT, int R0, int R1, int R2>
 struct ColCfg {
     static constexpr int cols = COLS, n = R0 * R1 * R2;
-    static size_t smem() { return (size_t)n * COLS * sizeof(cpx<T>) + (size_t)n * sizeof(TwPair<T>); }
+    static size_t smem(int = 0) { return (size_t)n * COLS * sizeof(cpx<T>) + (size_t)n * sizeof(TwPair<T>); }
     static cudaError_t configure(int optin) {
         cudaError_t e;
         if ((e = allow_max_dynamic_smem(k_col_fast<T, COLS, NT, R0, R1, R2, 0>, optin))) return e;
@@ -744,9 +801,9 @@ struct ColCfg {
         return allow_max_dynamic_smem(k_col_fast<T, COLS, NT, R0, R1, R2, 2>, optin);
     }
     static void launch(int mode, unsigned grid, const FastArgs<T>& a, cudaStream_t s) {
-        if (mode == 0) k_col_fast<T, COLS, NT, R0, R1, R2, 0><<<grid, NT, smem(), s>>>(a);
-        if (mode == 1) k_col_fast<T, COLS, NT, R0, R1, R2, 1><<<grid, NT, smem(), s>>>(a);
-        if (mode == 2) k_col_fast<T, COLS, NT, R0, R1, R2, 2><<<grid, NT, smem(), s>>>(a);
+        if (mode == 0) k_col_fast<T, COLS, NT, R0, R1, R2, 0><<<grid, NT, smem(0), s>>>(a);
+        if (mode == 1) k_col_fast<T, COLS, NT, R0, R1, R2, 1><<<grid, NT, smem(1), s>>>(a);
+        if (mode == 2) k_col_fast<T, COLS, NT, R0, R1, R2, 2><<<grid, NT, smem(2), s>>>(a);
     }
 };
 
@@ -846,8 +903,10 @@ int line_stream_variants(int m) { return m == 256 ? 2 : (with_line_stream_cfg(m,
 template <int NT, int R0, int R1, int R2, int NBUF, int COLS = 16, int MINB = 1>
 struct ColTmaCfg {
     static constexpr int cols = COLS, n = R0 * R1 * R2, minb = MINB;
-    static size_t smem() {  // tile ring, twiddles, mbarriers, reduction slots, alignment slack
-        return (size_t)NBUF * n * COLS * sizeof(cpx<float>) + (size_t)n * sizeof(TwPair<float>) + NBUF * 8 +
+    // tile ring, twiddles (MODE 2: the stage tables), mbarriers, reduction slots, alignment slack
+    static size_t smem(int mode = 2) {
+        const int tw = mode == 2 ? std::max(ColTwLayout<R0, R1, R2, 2>::total, n) : n;
+        return (size_t)NBUF * n * COLS * sizeof(cpx<float>) + (size_t)tw * sizeof(TwPair<float>) + NBUF * 8 +
                (NT / 32) * sizeof(double) + 1024;
     }
     // CTAs per SM the launch relies on: MINB, or fewer if they do not fit
@@ -856,11 +915,11 @@ struct ColTmaCfg {
         if (r[mode] == 0) {
             int b = 0;
             cudaError_t e = mode == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 0, NBUF, MINB>, NT, smem())
+                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 0, NBUF, MINB>, NT, smem(0))
                             : mode == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 1, NBUF, MINB>, NT, smem())
+                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 1, NBUF, MINB>, NT, smem(1))
                                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 2, NBUF, MINB>, NT, smem());
+                                              &b, k_col_tma<COLS, NT, R0, R1, R2, 2, NBUF, MINB>, NT, smem(2));
             if (e != cudaSuccess) cudaGetLastError();
             r[mode] = e == cudaSuccess && b > 0 ? (b < MINB ? b : MINB) : 1;
         }
@@ -875,11 +934,11 @@ struct ColTmaCfg {
     static void launch(int mode, unsigned grid, const FastArgs<float>& a, const CUtensorMap& map, int ntiles,
                        int chunks, int* err, cudaStream_t s) {
         if (mode == 0)
-            k_col_tma<COLS, NT, R0, R1, R2, 0, NBUF, MINB><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+            k_col_tma<COLS, NT, R0, R1, R2, 0, NBUF, MINB><<<grid, NT, smem(0), s>>>(a, map, ntiles, chunks, err);
         if (mode == 1)
-            k_col_tma<COLS, NT, R0, R1, R2, 1, NBUF, MINB><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+            k_col_tma<COLS, NT, R0, R1, R2, 1, NBUF, MINB><<<grid, NT, smem(1), s>>>(a, map, ntiles, chunks, err);
         if (mode == 2)
-            k_col_tma<COLS, NT, R0, R1, R2, 2, NBUF, MINB><<<grid, NT, smem(), s>>>(a, map, ntiles, chunks, err);
+            k_col_tma<COLS, NT, R0, R1, R2, 2, NBUF, MINB><<<grid, NT, smem(2), s>>>(a, map, ntiles, chunks, err);
     }
 };
 
