@@ -246,7 +246,11 @@ struct VecLoad<double, 2> {
     }
 };
 
-constexpr int kDepth = 4;  // slices of V in flight per thread in the force gather
+constexpr int kDepth = 4;         // slices of V in flight per thread in the force gather
+constexpr int kSlicesPerAdd = 4;  // slices summed plainly before one compensated add
+
+__device__ __forceinline__ float fmaf_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaf_t(double a, double b, double c) { return fma(a, b, c); }
 
 // Offset (elements of T) of the cp.async ring after the six weight rows of length ld, 16-byte aligned.
 template <typename T>
@@ -384,6 +388,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ?
         // ring of kDepth slices of this thread's pairs in shared memory, filled by
         // cp.async: each thread reads back only what it copied itself, so no barrier
         T* ring = wf + ring_offset<T>(ld);
+        T b0 = T(0), bx = T(0), by = T(0), bz = T(0);
         auto issue = [&](int t, int slot) {
             int ai = st[0] + t;
             if (ai >= n1) ai -= n1;
@@ -422,10 +427,18 @@ __global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ?
                 py += dwb[u] * r0;
                 pz += wb[u] * r1;
             }
-            kahan_add(s0, c0, wa[t] * p0);
-            kahan_add(sx, cx, dwa[t] * p0);
-            kahan_add(sy, cy, wa[t] * py);
-            kahan_add(sz, cz, wa[t] * pz);
+            // plain sums over groups of kSlicesPerAdd slices, each group added with compensation
+            b0 = fmaf_t(wa[t], p0, b0);
+            bx = fmaf_t(dwa[t], p0, bx);
+            by = fmaf_t(wa[t], py, by);
+            bz = fmaf_t(wa[t], pz, bz);
+            if ((k + 1) % kSlicesPerAdd == 0 || t + 1 == ia1) {
+                kahan_add(s0, c0, b0);
+                kahan_add(sx, cx, bx);
+                kahan_add(sy, cy, by);
+                kahan_add(sz, cz, bz);
+                b0 = bx = by = bz = T(0);
+            }
         }
         cp_async_wait<0>();
     } else {
