@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int
         bmax[threadIdx.x] = INT_MIN;
     }
     __syncthreads();  // the boxes are visible to the whole CTA
-    const int runs = (a.fb + kRun - 1) / kRun;
+    const int runs = (a.fb + kRun<T>() - 1) / kRun<T>();
     const int ntask = (i1 - i0) * 3 * runs;
     for (int t = threadIdx.x; t < ntask; t += blockDim.x) atom_factors_one(a, (long long)i0 * 3 * runs + t);
     if (!bins) return;

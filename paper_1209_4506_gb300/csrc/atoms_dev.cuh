@@ -47,13 +47,21 @@ __device__ __forceinline__ void atom_prep_one(const AtomArgs<T>& a, int i) {
     a.prep[i] = p;
 }
 
-// One thread per (atom, axis, run of kRun box points): fac / dfac computed in
+// One thread per (atom, axis, run of kRun<T>() box points): fac / dfac computed in
 // FP64.  FP32 plans start each run with three exponentials and continue with
-// the exact ratio recurrence; FP64 plans evaluate every point directly.
-constexpr int kRun = 8;
+// the exact ratio recurrence; FP64 plans evaluate every point directly.  The
+// recurrence's relative error after m steps is about m^2 / 2 FP64 roundings
+// (2e-13 at m = 64), far below the single FP32 rounding of each value, so FP32
+// runs are long: FP64 arithmetic runs at a small fraction of the FP32 rate, and
+// the exponentials dominate the setup.
+template <typename T>
+__host__ __device__ constexpr int kRun() {
+    return sizeof(T) == 4 ? 64 : 8;
+}
 
 template <typename T>
 __device__ __forceinline__ void atom_factors_one(const AtomArgs<T>& a, long long t) {
+    constexpr int kRun = hartree::kRun<T>();
     const int runs = (a.fb + kRun - 1) / kRun;
     if (t >= 3LL * a.n * runs) return;
     const int i = (int)(t / (3 * runs));

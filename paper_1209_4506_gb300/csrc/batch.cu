@@ -208,7 +208,7 @@ extern "C" int hartree_batch_create(const hartree_desc* descs, const int* atom_c
         h.grid_off[c + 1] = h.grid_off[c] + (long long)p.n[0] * p.n[1] * p.n[2];
         h.atom_off[c + 1] = h.atom_off[c] + atom_counts[c];
         const int n = atom_counts[c];
-        const int runs = (p.box_max + kRun - 1) / kRun;
+        const int runs = (p.box_max + kRun<float>() - 1) / kRun<float>();
         bc.splat_tb = (p.n[1] + TB - 1) / TB;
         bc.splat_tc = (p.n[2] + TC - 1) / TC;
         const int tA = (p.n[0] + TA - 1) / TA;
