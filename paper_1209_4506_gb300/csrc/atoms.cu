@@ -220,10 +220,15 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
 // Vector of VW consecutive values along c, loaded with one 8- or 16-byte access.
 template <typename T, int VW>
 struct VecLoad;
+// ld: from global memory (read-only path); lds: from shared memory (p aligned to the vector).
 template <>
 struct VecLoad<float, 4> {
     static __device__ __forceinline__ void ld(const float* p, float* v) {
         const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+    }
+    static __device__ __forceinline__ void lds(const float* p, float* v) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
         v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
     }
 };
@@ -233,15 +238,24 @@ struct VecLoad<float, 2> {
         const float2 x = __ldg(reinterpret_cast<const float2*>(p));
         v[0] = x.x, v[1] = x.y;
     }
+    static __device__ __forceinline__ void lds(const float* p, float* v) {
+        const float2 x = *reinterpret_cast<const float2*>(p);
+        v[0] = x.x, v[1] = x.y;
+    }
 };
 template <typename T>
 struct VecLoad<T, 1> {
     static __device__ __forceinline__ void ld(const T* p, T* v) { v[0] = __ldg(p); }
+    static __device__ __forceinline__ void lds(const T* p, T* v) { v[0] = *p; }
 };
 template <>
 struct VecLoad<double, 2> {
     static __device__ __forceinline__ void ld(const double* p, double* v) {
         const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+        v[0] = x.x, v[1] = x.y;
+    }
+    static __device__ __forceinline__ void lds(const double* p, double* v) {
+        const double2 x = *reinterpret_cast<const double2*>(p);
         v[0] = x.x, v[1] = x.y;
     }
 };
@@ -339,7 +353,7 @@ struct CGroups {
 // flight, not by arithmetic: each thread keeps kDepth slices of its pairs in
 // flight with cp.async copies into a private ring in shared memory.
 template <typename T, int VW, int KP, int NT>
-__global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ? 4 : 3))
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ? 4 : 3))
     k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs, double* __restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int fb = a.fb;
@@ -386,37 +400,46 @@ __global__ void __launch_bounds__(NT, NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ?
             }
         }
         // ring of kDepth slices of this thread's pairs in shared memory, filled by
-        // cp.async: each thread reads back only what it copied itself, so no barrier
+        // cp.async: each thread reads back only what it copied itself, so no barrier.
+        // Slot s, pair u of this thread sits at ring + ((s KP + u) NT + tid) VW.
         T* ring = wf + ring_offset<T>(ld);
-        T b0 = T(0), bx = T(0), by = T(0), bz = T(0);
-        auto issue = [&](int t, int slot) {
-            int ai = st[0] + t;
-            if (ai >= n1) ai -= n1;
-            const T* Vs = V + ai * slice;
+        constexpr uint32_t kPairBytes = NT * VW * sizeof(T), kSlotBytes = KP * kPairBytes;
+        const uint32_t ring_s = smem_u32(ring) + threadIdx.x * (uint32_t)(VW * sizeof(T));
+        int nbytes[KP];
 #pragma unroll
-            for (int u = 0; u < KP; ++u) {
-                const bool ok = threadIdx.x + NT * u < npairs;
-                cp_async<VW * sizeof(T)>(ring + ((slot * KP + u) * NT + threadIdx.x) * VW, Vs + off[u],
-                                         ok ? (int)(VW * sizeof(T)) : 0);
+        for (int u = 0; u < KP; ++u) nbytes[u] = threadIdx.x + NT * u < npairs ? (int)(VW * sizeof(T)) : 0;
+        T b0 = T(0), bx = T(0), by = T(0), bz = T(0);
+        // the next slice to issue: its a index and first element, advanced (with the periodic wrap) per issue
+        int ai = st[0] + ia0;
+        if (ai >= n1) ai -= n1;
+        const T* Vs = V + ai * slice;
+        auto issue = [&](uint32_t slot) {
+            const uint32_t d = ring_s + slot * kSlotBytes;
+#pragma unroll
+            for (int u = 0; u < KP; ++u) cp_async_s<VW * sizeof(T)>(d + u * kPairBytes, Vs + off[u], nbytes[u]);
+            if (++ai == n1) {
+                ai = 0;
+                Vs = V;
+            } else {
+                Vs += slice;
             }
         };
 #pragma unroll
         for (int k = 0; k < kDepth - 1; ++k) {
-            if (ia0 + k < ia1) issue(ia0 + k, k);
+            if (ia0 + k < ia1) issue((uint32_t)k);
             cp_async_commit();
         }
         for (int t = ia0; t < ia1; ++t) {
-            const int k = t - ia0;
-            if (t + kDepth - 1 < ia1) issue(t + kDepth - 1, (k + kDepth - 1) % kDepth);
+            const unsigned k = (unsigned)(t - ia0);
+            if (t + kDepth - 1 < ia1) issue((k + kDepth - 1) % kDepth);
             cp_async_commit();
             cp_async_wait<kDepth - 1>();  // the group of slice t is complete
-            const T* r = ring + (k % kDepth) * KP * NT * VW;
+            const T* r = ring + ((k % kDepth) * KP * NT + threadIdx.x) * VW;
             T p0 = T(0), py = T(0), pz = T(0);
 #pragma unroll
             for (int u = 0; u < KP; ++u) {
                 T v[VW];
-#pragma unroll
-                for (int e = 0; e < VW; ++e) v[e] = r[(u * NT + threadIdx.x) * VW + e];
+                VecLoad<T, VW>::lds(r + u * NT * VW, v);
                 T r0 = T(0), r1 = T(0);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {

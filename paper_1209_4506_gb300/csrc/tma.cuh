@@ -107,6 +107,15 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src, int src_byt
                      "r"(src_bytes)
                      : "memory");
 }
+// the same with the destination given as a shared-memory address
+template <int BYTES>
+__device__ __forceinline__ void cp_async_s(uint32_t dst, const void* src, int src_bytes) {
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(BYTES), "r"(src_bytes)
+                     : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // wait until at most N of this thread's committed copy groups are still pending
 template <int N>
