@@ -223,10 +223,11 @@ int hartree_plan_device_status(hartree_plan plan);
  * variants each (plain tiles, then bulk-copy streams) and V * V picks: a pick
  * v < V runs both c passes on variant v, a pick V + m runs the r2c pass on
  * variant m / (V - 1) and the c2r pass on one of the other V - 1 variants.
+ * The b passes pair their forward and inverse variants the same way.
  * hartree_plan_autotune times every variant on the plan's own workspace
  * (overwriting it; waits for the stream; not capturable) and keeps the
- * fastest, the r2c and c2r passes each on its own; choice[3] (host, may be
- * NULL) receives the picks.  hartree_plan_set_variants applies picks saved
+ * fastest, each pass of a pair on its own; choice[3] (host, may be NULL)
+ * receives the picks.  hartree_plan_set_variants applies picks saved
  * earlier (e.g. from a cache); out-of-range picks return HARTREE_ERR_INVALID.
  * Variants 0..2 apply the same operations to each element, so V_H is
  * identical across them; the radix-32 variants round differently; every

@@ -467,41 +467,41 @@ int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice) {
         if (r == cudaSuccess) r = cudaEventElapsedTime(ms, e0, e1);
         return r;
     };
-    // c passes: each of r2c and c2r takes its own fastest variant
-    const int V = c_single_variants(p);
-    if (V > 1 && e == cudaSuccess) {
+    // c and b passes: each of the pair (r2c / c2r, forward / inverse) takes its own fastest variant
+    static const int pair_passes[2][2] = {{0, 4}, {1, 3}};
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (k == 1 && p.prec == HARTREE_FP32_TC_SPLIT) continue;  // b passes run on the tensor cores
+        const int V = single_variants(p, k);
+        if (V <= 1) continue;
         int best_v[2] = {0, 0};
         for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
             float best = 1e30f;
             for (int v = 0; v < V && e == cudaSuccess; ++v) {
-                p.var[0] = v;
+                p.var[k] = v;
                 float ms = 0.f;
-                e = time_passes(q == 0 ? 0 : 4, -1, &ms);
+                e = time_passes(pair_passes[k][q], -1, &ms);
                 if (e == cudaSuccess && ms < best) {
                     best = ms;
                     best_v[q] = v;
                 }
             }
         }
-        p.var[0] = c_variant_index(V, best_v[0], best_v[1]);
+        p.var[k] = pair_index(V, best_v[0], best_v[1]);
     }
-    static const int passes[3][2] = {{0, 4}, {1, 3}, {2, -1}};
-    for (int k = 1; k < 3 && e == cudaSuccess; ++k) {
-        if (k == 1 && p.prec == HARTREE_FP32_TC_SPLIT) continue;  // b passes run on the tensor cores
-        const int nv = fast_variants(p, k);
-        if (nv <= 1) continue;
+    // the a pass
+    if (e == cudaSuccess && fast_variants(p, 2) > 1) {
         float best = 1e30f;
         int best_v = 0;
-        for (int v = 0; v < nv && e == cudaSuccess; ++v) {
-            p.var[k] = v;
+        for (int v = 0; v < fast_variants(p, 2) && e == cudaSuccess; ++v) {
+            p.var[2] = v;
             float ms = 0.f;
-            e = time_passes(passes[k][0], passes[k][1], &ms);
+            e = time_passes(2, -1, &ms);
             if (e == cudaSuccess && ms < best) {
                 best = ms;
                 best_v = v;
             }
         }
-        p.var[k] = best_v;
+        p.var[2] = best_v;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -1054,8 +1054,9 @@ bool line_stream_available(const Plan& p) {
     return p.M % 2 == 0 || ((long long)p.n[0] * p.n[1]) % lines == 0;
 }
 
+// Arguments of pass `pass` (its b-pass tiles follow that pass's own variant).
 template <typename T>
-FastArgs<T> make_fast_args(const Plan& p) {
+FastArgs<T> make_fast_args(const Plan& p, int pass) {
     FastArgs<T> a;
     a.n1 = p.n[0];
     a.n2 = p.n[1];
@@ -1075,7 +1076,7 @@ FastArgs<T> make_fast_args(const Plan& p) {
     a.a_chunks = 1;
     a.b_chunks = 1;
     with_col_cfg<T>(p.n[0], p.var[2], [&](auto c) { a.a_chunks = (p.nh + c.cols - 1) / c.cols; });
-    with_col_cfg<T>(p.n[1], p.var[1], [&](auto c) { a.b_chunks = (p.nh + c.cols - 1) / c.cols; });
+    with_col_cfg<T>(p.n[1], pass_variant(p, pass == 3 ? 3 : 1), [&](auto c) { a.b_chunks = (p.nh + c.cols - 1) / c.cols; });
     return a;
 }
 
@@ -1133,12 +1134,10 @@ cudaError_t configure_fast_kernels(const Plan& p) {
 // Returns the number of CTAs launched (the a pass's E_H partial count), or -1 if not specialised.
 template <typename T>
 long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s) {
-    FastArgs<T> a = make_fast_args<T>(p);
+    FastArgs<T> a = make_fast_args<T>(p, pass);
     long long grid = -1;
     if (pass == 0 || pass == 4) {
-        int vr = 0, vc = 0;
-        c_pass_variants(c_single_variants(p), p.var[0], &vr, &vc);
-        const int v = pass == 0 ? vr : vc;
+        const int v = pass_variant(p, pass);
         if constexpr (sizeof(T) == 4) {
             const void* grid_ptr = pass == 0 ? rho : vh;
             const int sv = v - line_variants(p.M);
@@ -1157,9 +1156,8 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
         return grid;
     }
     const int axis = (pass == 2) ? 0 : 1;  // transformed axis: a for pass 2, b for passes 1 and 3
-    const int kind = (pass == 2) ? 2 : 1;
     if constexpr (sizeof(T) == 4) {
-        const int tv = p.var[kind] - col_variants(p.n[axis]);
+        const int tv = pass_variant(p, pass) - col_variants(p.n[axis]);
         if (tv >= 0 && col_tma_available(p, axis)) {
             // TMA-streamed persistent kernel, one CTA per SM
             with_col_tma_cfg(p.n[axis], tv, [&](auto c) {
@@ -1175,7 +1173,7 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
             return grid;
         }
     }
-    with_col_cfg<T>(p.n[axis], p.var[kind], [&](auto c) {
+    with_col_cfg<T>(p.n[axis], pass_variant(p, pass), [&](auto c) {
         grid = (long long)p.n[1 - axis] * (axis == 0 ? a.a_chunks : a.b_chunks);
         c.launch(pass == 2 ? 2 : (pass == 3 ? 1 : 0), (unsigned)grid, a, s);
     });
@@ -1187,33 +1185,42 @@ long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, c
                                   : launch_fast_pass_t<float>(p, pass, rho, vh, s);
 }
 
-int c_single_variants(const Plan& p) {
-    return (p.use_fast & 1) ? line_variants(p.M) + (line_stream_available(p) ? line_stream_variants(p.M) : 0) : 1;
-}
-
-void c_pass_variants(int V, int v, int* v_r2c, int* v_c2r) {
-    if (v < V || V < 2) {
-        *v_r2c = *v_c2r = v < V ? v : 0;
-        return;
-    }
-    const int m = v - V, r = m / (V - 1), c = m % (V - 1);
-    *v_r2c = r;
-    *v_c2r = c < r ? c : c + 1;
-}
-
-int c_variant_index(int V, int v_r2c, int v_c2r) {
-    if (v_r2c == v_c2r) return v_r2c;
-    return V + v_r2c * (V - 1) + (v_c2r < v_r2c ? v_c2r : v_c2r - 1);
-}
-
-int fast_variants(const Plan& p, int kind) {
-    if (kind == 0) {
-        const int V = c_single_variants(p);
-        return V * V;
-    }
+int single_variants(const Plan& p, int kind) {
+    if (kind == 0)
+        return (p.use_fast & 1) ? line_variants(p.M) + (line_stream_available(p) ? line_stream_variants(p.M) : 0)
+                                : 1;
     const int ax = kind == 1 ? 1 : 0;
     if (!(p.use_fast & (kind == 1 ? 2 : 4))) return 1;
     return col_variants(p.n[ax]) + (col_tma_available(p, ax) ? col_tma_variants(p.n[ax]) : 0);
+}
+
+void pair_variants(int V, int v, int* first, int* second) {
+    if (v < V || V < 2) {
+        *first = *second = v < V ? v : 0;
+        return;
+    }
+    const int m = v - V, r = m / (V - 1), c = m % (V - 1);
+    *first = r;
+    *second = c < r ? c : c + 1;
+}
+
+int pair_index(int V, int first, int second) {
+    if (first == second) return first;
+    return V + first * (V - 1) + (second < first ? second : second - 1);
+}
+
+int fast_variants(const Plan& p, int kind) {
+    const int V = single_variants(p, kind);
+    return kind == 2 ? V : V * V;
+}
+
+// The variant pass `pass` (0..4) runs under the plan's picks.
+int pass_variant(const Plan& p, int pass) {
+    if (pass == 2) return p.var[2];
+    const int kind = (pass == 0 || pass == 4) ? 0 : 1;
+    int first = 0, second = 0;
+    pair_variants(single_variants(p, kind), p.var[kind], &first, &second);
+    return (pass == 0 || pass == 1) ? first : second;
 }
 
 // ------------------------------------------------------------------ host: tensor maps

@@ -225,11 +225,13 @@ cudaError_t configure_poisson_kernels(const Plan& p);
 cudaError_t configure_fast_kernels(const Plan& p);
 int fast_pass_mask(const Plan& p);
 int fast_variants(const Plan& p, int kind);  // kind 0: c passes, 1: b passes, 2: a pass
-// The c passes' variant index v: below the single-pass variant count V both c passes take v;
-// V + m pairs r2c variant m / (V - 1) with one of the other V - 1 c2r variants.
-int c_single_variants(const Plan& p);
-void c_pass_variants(int V, int v, int* v_r2c, int* v_c2r);
-int c_variant_index(int V, int v_r2c, int v_c2r);
+// Pass kinds 0 (c: r2c, c2r) and 1 (b: forward, inverse) pick a variant per pass.  Their
+// variant index v: below the single-pass variant count V both passes take v; V + m pairs
+// the first pass's variant m / (V - 1) with one of the other V - 1 variants for the second.
+int single_variants(const Plan& p, int kind);
+void pair_variants(int V, int v, int* first, int* second);
+int pair_index(int V, int first, int second);
+int pass_variant(const Plan& p, int pass);  // the variant pass 0..4 runs under the plan's picks
 void prepare_tma(Plan& p);                   // encode the tensor maps of the TMA-streamed passes
 long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
 cudaError_t configure_atom_kernels(const Plan& p);

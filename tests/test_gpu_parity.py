@@ -264,6 +264,21 @@ def test_force_gather_row_residues(precision, n):
     assert np.max(np.abs(g["phi"] - ref["phi"])) <= tol["f"]
 
 
+def test_fp32_factor_runs_longer_than_one_recurrence():
+    """FP32 boxes of more than 64 points per axis: the 1D factors are built in several runs of
+    the FP64 ratio recurrence (each restarted from exponentials); rho, V_H and the forces still
+    match the oracle.  Cell 6 x 6.25 x 7 Bohr on 96 x 100 x 112 (h = 0.0625 Bohr), sigma 0.6 Bohr,
+    5 sigma cutoff: 97 points per axis."""
+    S = synth.random_system((96, 100, 112), (6.0, 6.25, 7.0), 6, 0.6, seed=4242, precision="fp32")
+    ref = O.solve_system(S, rc_sigmas=5.0)
+    g = gpu_step(S, "fp32", cutoff_sigmas=5.0)
+    tol = TOL["fp32"]
+    assert rel_l2(g["rho"], ref["rho"]) <= tol["v"]
+    assert rel_l2(g["vh"], ref["vh"]) <= tol["v"]
+    assert abs(g["eh"] - ref["eh"]) <= tol["e"] * abs(ref["eh"])
+    assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
+
+
 def test_forces_recompute_when_vh_is_null():
     S, ref = oracle_cfg("cfg2")
     plan = HartreePlan(S.n, S.cell, S.sigma, "fp32")
