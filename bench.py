@@ -132,6 +132,23 @@ SAMPLE_TEXT = ("oracle step (splat 5 sigma, FP64 Poisson, E_H, forces) on the 4x
                "256^3 grid (same density and sigma as the 512^3 workload); GB/s on its own 40 N_tot yardstick")
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (x itself on one rank): the job's time is its slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ybytes, steps, seconds, world):
+    """Whole-job GB/s: every rank runs its own replica of the workload (weak scaling)."""
+    return world * ybytes * steps / seconds / 1e9
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -289,7 +306,6 @@ def adjoint_section(plan, pos, q, rho, vh, stream, reps, plain_solve_ms):
 def side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrier, ybytes, plain_solve_ms, dev):
     """e2e through the C ABI with host buffers, the adjoint forms and the batched form."""
     import torch
-    import torch.distributed as dist
 
     # end to end: pinned host buffers in, host results out, copies and read-back inside the timed region
     pos_pin = torch.tensor(pos_h).pin_memory()
@@ -301,12 +317,8 @@ def side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrie
     t0 = time.perf_counter()
     for _ in range(n_e2e):
         plan.step_host(pos_pin.numpy(), q_pin.numpy())
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = {"value": world * ybytes * n_e2e / t_e2e / 1e9, "unit": "GB/s",
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": job_throughput(ybytes, n_e2e, t_e2e, world), "unit": "GB/s",
            "h2d_bytes_per_step": int(pos_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(8 + pos_h.nbytes),
            "ms_per_step": 1e3 * t_e2e / n_e2e, "api": "hartree_step_host"}
     side_reps = max(5, min(args.steps, 50))
@@ -394,13 +406,9 @@ def main():
     barrier()
     clocks = sampler.stop()
     launches = plan.launch_count - launches0
-    t_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_per_step = t_ms / args.steps
-    value = world * ybytes * args.steps / (t_ms * 1e-3) / 1e9
+    value = job_throughput(ybytes, args.steps, t_ms * 1e-3, world)
 
     # per-kernel durations from CUDA events on the launching stream (same kernels, split calls)
     names = ["splat", "pass0_c_r2c", "pass1_b_fwd", "pass2_a_green", "pass3_b_inv", "pass4_c_c2r", "forces"]
