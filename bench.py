@@ -12,8 +12,9 @@ value: HBM yardstick bytes per step (40 N_tot, the five read+write sweeps of
 the Poisson solve) x steps / time, summed over ranks ("GB/s", higher is
 better).  ms_per_step, solve_ms and the per-kernel breakdown sit beside it.
 
---impl reference times the FP64 CPU oracle (the reference for this build) on
-the host cores, on a bounded 256^3 sample of the same system.
+--impl reference times the FP64 CPU oracle (the paper's method written out
+plainly, the library's parity reference) on the host cores, on a bounded 256^3
+sample of the same system.
 Multi-GPU: one replica per GPU (the single grid does not shard without an
 all-to-all; replicas run independent workloads), launched with torchrun.
 """
