@@ -354,7 +354,8 @@ struct CGroups {
 // flight with cp.async copies into a private ring in shared memory.
 template <typename T, int VW, int KP, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : NT == 128 ? (KP <= 5 ? 5 : 4) : (KP <= 2 ? 4 : 3))
-    k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs, double* __restrict__ part) {
+    k_forces(AtomArgs<T> a, const T* __restrict__ V, int slabs, double* __restrict__ part, double* __restrict__ f,
+             double* __restrict__ phi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int fb = a.fb;
     const int ld = fb + 8;
@@ -497,9 +498,20 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : NT == 128 ? (KP <= 5 
     }
     // four block sums: error-free FP32 warp steps, FP64 only across warps
     const T vs[4] = {s0, sx, sy, sz}, ve[4] = {-c0, -cx, -cy, -cz};
-    for (int c = 0; c < 4; ++c) {
-        const double tot = block_sum_comp(vs[c], ve[c], red[c]);
-        if (threadIdx.x == 0) part[(long long)blockIdx.x * 4 + c] = tot;
+    double tot[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tot[c] = block_sum_comp(vs[c], ve[c], red[c]);
+    if (threadIdx.x != 0) return;
+    if (f) {
+        // one slab per atom: the forces and phi directly, as k_forces_finalize forms them
+        const double cf = -a.dV * a.q[atom] * a.norm * 2.0 * a.inv_s2;
+        f[3 * atom + 0] = cf * tot[1];
+        f[3 * atom + 1] = cf * tot[2];
+        f[3 * atom + 2] = cf * tot[3];
+        if (phi) phi[atom] = a.dV * a.norm * tot[0];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[(long long)blockIdx.x * 4 + c] = tot[c];
     }
 }
 
@@ -558,50 +570,52 @@ size_t forces_smem(const Plan& p, size_t real_size, int vw, ForceShape fs);
 
 template <typename T, int VW, int NT>
 void launch_k_forces_nt(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs, int kp,
-                        size_t sm, cudaStream_t s) {
+                        size_t sm, double* f, double* phi, cudaStream_t s) {
     if constexpr (NT == 128) {
         switch (kp) {
-            case 5: k_forces<T, VW, 5, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); return;
-            case 6: k_forces<T, VW, 6, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); return;
+            case 5: k_forces<T, VW, 5, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials, f, phi); return;
+            case 6: k_forces<T, VW, 6, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials, f, phi); return;
             default: break;
         }
     }
     switch (kp) {
-        case 1: k_forces<T, VW, 1, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); break;
-        case 2: k_forces<T, VW, 2, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); break;
-        case 3: k_forces<T, VW, 3, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); break;
-        default: k_forces<T, VW, 4, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials); break;
+        case 1: k_forces<T, VW, 1, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials, f, phi); break;
+        case 2: k_forces<T, VW, 2, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials, f, phi); break;
+        case 3: k_forces<T, VW, 3, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials, f, phi); break;
+        default: k_forces<T, VW, 4, NT><<<blocks, NT, sm, s>>>(a, V, slabs, p.force_partials, f, phi); break;
     }
 }
 
 // Pairs per thread: enough for the largest box of the plan (npairs <= box_max x
 // (box_max + 2 VW) / VW); boxes beyond that loop over the pairs from shared memory.
 template <typename T, int VW>
-void launch_k_forces_vw(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs,
-                        cudaStream_t s) {
+void launch_k_forces_vw(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs, double* f,
+                        double* phi, cudaStream_t s) {
     const ForceShape fs = forces_shape(p, VW);
     const size_t sm = forces_smem(p, sizeof(T), VW, fs);
     if constexpr (sizeof(T) == 4 && VW == 4)
-        if (fs.nt == 128) return launch_k_forces_nt<T, VW, 128>(p, a, V, blocks, slabs, fs.kp, sm, s);
-    launch_k_forces_nt<T, VW, kThreads>(p, a, V, blocks, slabs, fs.kp, sm, s);
+        if (fs.nt == 128) return launch_k_forces_nt<T, VW, 128>(p, a, V, blocks, slabs, fs.kp, sm, f, phi, s);
+    launch_k_forces_nt<T, VW, kThreads>(p, a, V, blocks, slabs, fs.kp, sm, f, phi, s);
 }
 
 // The widest aligned vector along c: V must be VW-element aligned and VW must divide N2 N3
-// (every a slice then starts aligned; CGroups handles rows of any residue).
+// (every a slice then starts aligned; CGroups handles rows of any residue).  f, phi: written
+// directly by a one-slab launch (else null: partials for k_forces_finalize).
 template <typename T>
-void launch_k_forces(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs, cudaStream_t s) {
+void launch_k_forces(const Plan& p, const AtomArgs<T>& a, const T* V, unsigned blocks, int slabs, double* f,
+                     double* phi, cudaStream_t s) {
     const uintptr_t addr = reinterpret_cast<uintptr_t>(V);
     const long long slice = (long long)p.n[1] * p.n[2];
     if constexpr (sizeof(T) == 4) {
         if (slice % 4 == 0 && addr % 16 == 0) {
-            launch_k_forces_vw<T, 4>(p, a, V, blocks, slabs, s);
+            launch_k_forces_vw<T, 4>(p, a, V, blocks, slabs, f, phi, s);
             return;
         }
     }
     if (slice % 2 == 0 && addr % (2 * sizeof(T)) == 0)
-        launch_k_forces_vw<T, 2>(p, a, V, blocks, slabs, s);
+        launch_k_forces_vw<T, 2>(p, a, V, blocks, slabs, f, phi, s);
     else
-        launch_k_forces_vw<T, 1>(p, a, V, blocks, slabs, s);
+        launch_k_forces_vw<T, 1>(p, a, V, blocks, slabs, f, phi, s);
 }
 
 size_t forces_smem(const Plan& p, size_t real_size, int vw, ForceShape fs) {
@@ -630,11 +644,16 @@ cudaError_t forces_impl(const Plan& p, const double* pos, const double* q, int n
         cudaError_t e = prep_atoms<T>(p, a, false, s);
         if (e != cudaSuccess) return e;
     }
-    p.launches += 2;
     int slabs = (4 * 152 * 2 + n - 1) / n;  // enough CTAs to cover the GPU
     if (slabs > p.max_force_slabs) slabs = p.max_force_slabs;
     if (slabs < 1) slabs = 1;
-    launch_k_forces<T>(p, a, static_cast<const T*>(vh), (unsigned)n * slabs, slabs, s);
+    if (slabs == 1) {  // one CTA per atom writes its forces: no partials, no finalize launch
+        p.launches += 1;
+        launch_k_forces<T>(p, a, static_cast<const T*>(vh), (unsigned)n, 1, f, phi, s);
+        return cudaGetLastError();
+    }
+    p.launches += 2;
+    launch_k_forces<T>(p, a, static_cast<const T*>(vh), (unsigned)n * slabs, slabs, nullptr, nullptr, s);
     k_forces_finalize<<<(n + 127) / 128, 128, 0, s>>>(p.force_partials, n, slabs, q, p.dV, a.norm, a.inv_s2, f, phi);
     return cudaGetLastError();
 }
