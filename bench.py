@@ -470,7 +470,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32, b passes f16x2-split",
+            "data": "synthetic",
             "config": {"workload": wl_text + (", FP32" if args.precision == "fp32" else
                                               ", FP32 with tensor-core split b passes") +
                                    ": splat + Poisson + E_H + forces",
