@@ -30,13 +30,6 @@ int cuda_fail(cudaError_t e, const char* where) {
     return fail(HARTREE_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-bool smooth_size(int n) {  // 2/3/5/7-smooth
-    if (n < 1) return false;
-    for (int p : {2, 3, 5, 7})
-        while (n % p == 0) n /= p;
-    return n == 1;
-}
-
 // Radices for a line of length n: powers of two in balanced stages of at
 // most 16, then the factors 3, 5 and 7 one stage each.
 bool make_radix_plan(int n, RadixPlan* rp) {
@@ -149,6 +142,57 @@ bool finite_pos(double x) { return std::isfinite(x); }
 
 void hartree::set_last_error(const char* msg) { g_last_error = msg; }
 
+bool hartree::smooth_size(int n) {  // 2/3/5/7-smooth
+    if (n < 1) return false;
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Grid geometry, radix plans and pass tiling: everything the Poisson passes read from a plan
+// besides its device buffers.  hartree_plan_create and the allocation-free solve both build
+// their plans with it, so the two run the same passes with the same tiles.
+int hartree::init_plan_geometry(Plan& p, const hartree_desc& d) {
+    p.desc = d;
+    p.prec = d.precision;
+    p.real_size = p.prec == HARTREE_FP64 ? sizeof(double) : sizeof(float);
+    for (int i = 0; i < 3; ++i) {
+        p.n[i] = d.n[i];
+        p.L[i] = d.cell[i];
+        p.h[i] = d.cell[i] / d.n[i];
+    }
+    p.M = p.n[2] / 2;
+    p.nh = p.M + 1;
+    {
+        const int align = p.prec == HARTREE_FP64 ? 8 : 16;  // 128-byte rows
+        p.ldc = (p.nh + align - 1) / align * align;
+    }
+    p.omega = p.L[0] * p.L[1] * p.L[2];
+    p.dV = p.omega / ((double)p.n[0] * p.n[1] * p.n[2]);
+    for (int i = 0; i < 3; ++i) {
+        const int len = i == 2 ? p.M : p.n[i];
+        if (!make_radix_plan(len, &p.rp[i]))
+            return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan: no radix plan for length %d", len);
+    }
+    // tiling of the generic passes: two ping-pong buffers per CTA, about 64 KB of shared memory
+    const size_t cs = 2 * p.real_size;  // complex element
+    const size_t budget = 64 * 1024;
+    p.c_lines = (int)(budget / (2 * (size_t)(p.M + 1) * cs)) - 1;
+    if (p.c_lines > 32) p.c_lines = 32;
+    if (p.c_lines < 2) p.c_lines = 2;
+    p.c_lines &= ~1;  // even, so the padded leading dimension L + 1 is odd
+    p.b_cols = (int)(budget / (2 * (size_t)p.n[1] * cs));
+    p.a_cols = (int)(budget / (2 * (size_t)p.n[0] * cs));
+    p.b_cols = p.b_cols > 16 ? 16 : (p.b_cols < 1 ? 1 : p.b_cols);
+    p.a_cols = p.a_cols > 16 ? 16 : (p.a_cols < 1 ? 1 : p.a_cols);
+    p.smem_c = 2 * (size_t)(p.M + 1) * (p.c_lines + 1) * cs;
+    p.smem_b = 2 * (size_t)p.n[1] * p.b_cols * cs;
+    p.smem_a = 2 * (size_t)p.n[0] * p.a_cols * cs;
+    p.n_eh_partials = p.n[1] * p.nh;  // enough for one a-pass CTA per (b, column)
+    p.use_fast = fast_pass_mask(p);
+    return HARTREE_OK;
+}
+
 extern "C" {
 
 const char* hartree_status_string(int status) {
@@ -192,28 +236,19 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
     hartree_plan_s* h = new (std::nothrow) hartree_plan_s();
     if (!h) return fail(HARTREE_ERR_OOM, "plan_create: host allocation failed");
     Plan& p = h->p;
-    p.desc = d;
-    p.prec = d.precision;
-    p.real_size = p.prec == HARTREE_FP64 ? sizeof(double) : sizeof(float);
-    for (int i = 0; i < 3; ++i) {
-        p.n[i] = d.n[i];
-        p.L[i] = d.cell[i];
-        p.h[i] = d.cell[i] / d.n[i];
+    {
+        const int st = init_plan_geometry(p, d);
+        if (st != HARTREE_OK) {
+            delete h;
+            return st;
+        }
     }
     if (p.prec == HARTREE_FP32_TC_SPLIT && !tc_split_supported(p)) {
         delete h;
         return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: HARTREE_FP32_TC_SPLIT needs N2 = 256 (got %d)", p.n[1]);
     }
-    p.M = p.n[2] / 2;
-    p.nh = p.M + 1;
-    {
-        const int align = p.prec == HARTREE_FP64 ? 8 : 16;  // 128-byte rows
-        p.ldc = (p.nh + align - 1) / align * align;
-    }
     p.sigma = d.sigma;
     p.rc = (d.cutoff_sigmas > 0.0 ? d.cutoff_sigmas : (p.prec == HARTREE_FP64 ? 8.0 : 5.0)) * d.sigma;
-    p.omega = p.L[0] * p.L[1] * p.L[2];
-    p.dV = p.omega / ((double)p.n[0] * p.n[1] * p.n[2]);
     p.apl = d.atoms_per_leaf > 0 ? d.atoms_per_leaf : 16;
     p.max_atoms = d.max_atoms > 0 ? d.max_atoms : 65536;
     p.max_leaves = (p.max_atoms + p.apl - 1) / p.apl;
@@ -227,29 +262,6 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: cutoff box spans %d > %d grid points", p.box_max,
                     kMaxBoxPoints);
     }
-    for (int i = 0; i < 3; ++i) {
-        const int len = i == 2 ? p.M : p.n[i];
-        if (!make_radix_plan(len, &p.rp[i])) {
-            delete h;
-            return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "plan_create: no radix plan for length %d", len);
-        }
-    }
-    // tiling: two ping-pong buffers per CTA, about 64 KB of shared memory
-    const size_t cs = 2 * p.real_size;  // complex element
-    const size_t budget = 64 * 1024;
-    p.c_lines = (int)(budget / (2 * (size_t)(p.M + 1) * cs)) - 1;
-    if (p.c_lines > 32) p.c_lines = 32;
-    if (p.c_lines < 2) p.c_lines = 2;
-    p.c_lines &= ~1;  // even, so the padded leading dimension L + 1 is odd
-    p.b_cols = (int)(budget / (2 * (size_t)p.n[1] * cs));
-    p.a_cols = (int)(budget / (2 * (size_t)p.n[0] * cs));
-    p.b_cols = p.b_cols > 16 ? 16 : (p.b_cols < 1 ? 1 : p.b_cols);
-    p.a_cols = p.a_cols > 16 ? 16 : (p.a_cols < 1 ? 1 : p.a_cols);
-    p.smem_c = 2 * (size_t)(p.M + 1) * (p.c_lines + 1) * cs;
-    p.smem_b = 2 * (size_t)p.n[1] * p.b_cols * cs;
-    p.smem_a = 2 * (size_t)p.n[0] * p.a_cols * cs;
-    p.n_eh_partials = p.n[1] * p.nh;  // enough for one a-pass CTA per (b, column)
-    p.use_fast = fast_pass_mask(p);
     p.max_force_slabs = 1216;
 
     {
@@ -258,6 +270,7 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         p.n_tiles = p.tiles[0] * p.tiles[1] * p.tiles[2];
     }
     const size_t ntot = (size_t)p.n[0] * p.n[1] * p.n[2];
+    const size_t cs = 2 * p.real_size;  // complex element
     struct Alloc {
         void** ptr;
         size_t bytes;

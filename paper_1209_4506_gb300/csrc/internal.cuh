@@ -221,6 +221,10 @@ cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int 
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
                           double* phi, cudaStream_t s, bool prepared = false);
 void set_last_error(const char* msg);  // the message hartree_last_error() returns on this thread
+// Grid geometry, radix plans and pass tiling of `p` from `d` (sizes already validated):
+// HARTREE_OK, or HARTREE_ERR_UNSUPPORTED_SIZE with the thread's message set.
+int init_plan_geometry(Plan& p, const hartree_desc& d);
+bool smooth_size(int n);  // n is 2/3/5/7-smooth
 cudaError_t configure_poisson_kernels(const Plan& p);
 cudaError_t configure_fast_kernels(const Plan& p);
 int fast_pass_mask(const Plan& p);
@@ -235,6 +239,11 @@ int pass_variant(const Plan& p, int pass);  // the variant pass 0..4 runs under 
 void prepare_tma(Plan& p);                   // encode the tensor maps of the TMA-streamed passes
 long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
 cudaError_t configure_atom_kernels(const Plan& p);
+// paired-lane TMA column passes (pair_passes.cu), FP32: b (passes 1, 3) and a (pass 2)
+int col_pair_variants(int n);
+bool col_pair_available(const Plan& p, int axis);
+cudaError_t configure_col_pair(const Plan& p, int optin);
+long long launch_col_pair(const Plan& p, int pass, int variant, const FastArgs<float>& a, cudaStream_t s);
 // tensor-core b passes of HARTREE_FP32_TC_SPLIT plans (tc_split.cu)
 bool tc_split_supported(const Plan& p);
 size_t tc_table_bytes();

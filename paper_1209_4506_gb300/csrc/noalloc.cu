@@ -12,7 +12,12 @@
 //
 // Host code cannot use the array's name as a device address (it names a
 // host-side stand-in), so the first call on each device looks the address up
-// with cudaGetSymbolAddress, with that device current, and keeps it.
+// with cudaGetSymbolAddress, with that device current, and keeps it together
+// with the identity of the CUDA context it belongs to.  If that context is
+// later torn down and another created (cudaDeviceReset, or the primary context
+// released and retained again), the module is loaded anew and the array may
+// move: a call that finds a different context looks the address up again.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -28,38 +33,45 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
+// Per device: the context the cached set-up belongs to (its process-unique ID), the scratch
+// array's address in it, and the precision and grid whose kernels were last configured there
+// (the kernels' shared-memory attributes; a new grid may use other kernels).
+struct NoAllocDevice {
+    unsigned long long ctx_id = 0;  // 0: nothing cached
+    void* addr = nullptr;
+    int conf[4] = {-1, 0, 0, 0};  // precision, N1, N2, N3 last configured (-1: none)
+};
 std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[kMaxDevices] = {};
+NoAllocDevice g_noalloc_dev[kMaxDevices];
 
 int noalloc_fail(int status, const char* msg) {
     set_last_error(msg);  // reported by hartree_last_error()
     return status;
 }
 
-bool smooth_na(int n) {  // 2/3/5/7-smooth
-    if (n < 1) return false;
-    for (int p : {2, 3, 5, 7})
-        while (n % p == 0) n /= p;
-    return n == 1;
-}
-
-bool radix_plan_na(int n, RadixPlan* rp) {
-    rp->n = n;
-    rp->nst = 0;
-    int e2 = 0, m = n, n3 = 0, n5 = 0, n7 = 0;
-    while (m % 2 == 0) m /= 2, ++e2;
-    while (m % 3 == 0) m /= 3, ++n3;
-    while (m % 5 == 0) m /= 5, ++n5;
-    while (m % 7 == 0) m /= 7, ++n7;
-    if (m != 1) return false;
-    if (e2 > 0) {
-        const int st = (e2 + 3) / 4;
-        for (int s = 0; s < st; ++s) rp->r[rp->nst++] = 1 << (e2 / st + (s < e2 % st ? 1 : 0));
+// The process-unique ID of the current CUDA context (driver entry points cuCtxGetCurrent and
+// cuCtxGetId, looked up through the runtime); false if there is none or the driver lacks them.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {  // called with g_noalloc_mutex held
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
     }
-    for (int i = 0; i < n3; ++i) rp->r[rp->nst++] = 3;
-    for (int i = 0; i < n5; ++i) rp->r[rp->nst++] = 5;
-    for (int i = 0; i < n7; ++i) rp->r[rp->nst++] = 7;
-    return rp->nst >= 1 && rp->nst <= kMaxStages;
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS && *id != 0;
 }
 
 // Twiddle tables (plain and high/low pairs) and |G|^2 pairs of one axis, in FP64 then rounded.
@@ -100,7 +112,7 @@ extern "C" int hartree_solve_density_noalloc(const hartree_desc* desc, const voi
     if (d.flags != 0 || (d.precision != HARTREE_FP64 && d.precision != HARTREE_FP32))
         return noalloc_fail(HARTREE_ERR_INVALID, "solve_density_noalloc: precision must be FP64 or FP32, flags 0");
     for (int i = 0; i < 3; ++i) {
-        if (d.n[i] < 2 || d.n[i] > kMaxAxis || !smooth_na(d.n[i]))
+        if (d.n[i] < 2 || d.n[i] > kMaxAxis || !smooth_size(d.n[i]))
             return noalloc_fail(HARTREE_ERR_UNSUPPORTED_SIZE, "solve_density_noalloc: a grid size is not 2/3/5/7-smooth");
         if (!(d.cell[i] > 0.0) || !std::isfinite(d.cell[i]))
             return noalloc_fail(HARTREE_ERR_INVALID, "solve_density_noalloc: cell sides must be positive");
@@ -113,37 +125,11 @@ extern "C" int hartree_solve_density_noalloc(const hartree_desc* desc, const voi
                                                             : "solve_density_noalloc: grids must be aligned to 8 bytes");
 
     Plan p;
-    p.desc = d;
-    p.prec = d.precision;
-    p.real_size = p.prec == HARTREE_FP64 ? sizeof(double) : sizeof(float);
-    const size_t cs = 2 * p.real_size;
-    for (int i = 0; i < 3; ++i) {
-        p.n[i] = d.n[i];
-        p.L[i] = d.cell[i];
-        p.h[i] = d.cell[i] / d.n[i];
+    {
+        const int st = init_plan_geometry(p, d);
+        if (st != HARTREE_OK) return st;
     }
-    p.M = p.n[2] / 2;
-    p.nh = p.M + 1;
-    const int align = p.prec == HARTREE_FP64 ? 8 : 16;
-    p.ldc = (p.nh + align - 1) / align * align;
-    p.omega = p.L[0] * p.L[1] * p.L[2];
-    p.dV = p.omega / ((double)p.n[0] * p.n[1] * p.n[2]);
-    for (int i = 0; i < 3; ++i)
-        if (!radix_plan_na(i == 2 ? p.M : p.n[i], &p.rp[i]))
-            return noalloc_fail(HARTREE_ERR_UNSUPPORTED_SIZE, "solve_density_noalloc: no radix plan");
-    const size_t budget = 64 * 1024;
-    p.c_lines = (int)(budget / (2 * (size_t)(p.M + 1) * cs)) - 1;
-    p.c_lines = p.c_lines > 32 ? 32 : (p.c_lines < 2 ? 2 : p.c_lines);
-    p.c_lines &= ~1;
-    p.b_cols = (int)(budget / (2 * (size_t)p.n[1] * cs));
-    p.a_cols = (int)(budget / (2 * (size_t)p.n[0] * cs));
-    p.b_cols = p.b_cols > 16 ? 16 : (p.b_cols < 1 ? 1 : p.b_cols);
-    p.a_cols = p.a_cols > 16 ? 16 : (p.a_cols < 1 ? 1 : p.a_cols);
-    p.smem_c = 2 * (size_t)(p.M + 1) * (p.c_lines + 1) * cs;
-    p.smem_b = 2 * (size_t)p.n[1] * p.b_cols * cs;
-    p.smem_a = 2 * (size_t)p.n[0] * p.a_cols * cs;
-    p.n_eh_partials = p.n[1] * p.nh;
-    p.use_fast = fast_pass_mask(p);
+    const size_t cs = 2 * p.real_size;
 
     // scratch layout: half spectrum, tables, E_H partials (each 256-byte aligned)
     const size_t sz_W = align256((size_t)p.n[0] * p.n[1] * p.ldc * cs);
@@ -161,22 +147,39 @@ extern "C" int hartree_solve_density_noalloc(const hartree_desc* desc, const voi
                             "solve_density_noalloc: the grid needs more than the 8 MiB static scratch "
                             "(half spectrum N1*N2*ceil16(N3/2+1)*8 bytes in FP32, *16 in FP64, plus tables)");
 
-    // set-up, once per device: the scratch array's device address
+    // set-up, once per device and context: the scratch array's device address and the kernels'
+    // shared-memory attributes
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(HARTREE_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(HARTREE_ERR_CUDA, "solve_density_noalloc: device ordinal");
     unsigned char* base = nullptr;
+    bool configured = false;
+    const int key[4] = {p.prec, p.n[0], p.n[1], p.n[2]};
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_addr[dev]) {
+        NoAllocDevice& nd = g_noalloc_dev[dev];
+        unsigned long long id = 0;
+        const bool have_id = current_context_id(&id);
+        if (!have_id || nd.ctx_id != id || !nd.addr) {
             void* ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);  // creates the context if there is none yet
             if (e != cudaSuccess || !ptr)
                 return noalloc_fail(HARTREE_ERR_CUDA, "solve_density_noalloc: cudaGetSymbolAddress failed");
-            g_noalloc_addr[dev] = ptr;
+            unsigned long long id2 = 0;
+            nd = NoAllocDevice{};
+            nd.addr = ptr;
+            nd.ctx_id = current_context_id(&id2) ? id2 : 0;  // 0: look the address up again next call
         }
-        base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+        base = static_cast<unsigned char*>(nd.addr);
+        configured = std::equal(key, key + 4, nd.conf);
+    }
+    if (!configured) {
+        e = configure_poisson_kernels(p);
+        if (e == cudaSuccess) e = configure_fast_kernels(p);
+        if (e != cudaSuccess) return noalloc_fail(HARTREE_ERR_CUDA, cudaGetErrorString(e));
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        std::copy(key, key + 4, g_noalloc_dev[dev].conf);
     }
     size_t off = 0;
     p.W = base + off;
@@ -190,10 +193,6 @@ extern "C" int hartree_solve_density_noalloc(const hartree_desc* desc, const voi
         off += sz_g[i];
     }
     p.eh_partials = reinterpret_cast<double*>(base + off);
-
-    e = configure_poisson_kernels(p);
-    if (e == cudaSuccess) e = configure_fast_kernels(p);
-    if (e != cudaSuccess) return noalloc_fail(HARTREE_ERR_CUDA, cudaGetErrorString(e));
 
     cudaStream_t s = (cudaStream_t)stream;
     for (int i = 0; i < 3; ++i) {

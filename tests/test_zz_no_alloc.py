@@ -6,17 +6,20 @@ allocation is not allowed or would stall other work.  For them the library
 offers a Poisson solve that needs no plan and allocates nothing; it works in a
 fixed 8 MiB scratch array that the library declares at file scope.
 
-These tests call that entry point through the C ABI twice in a row (FP32, then
-FP64, then FP32 again on the shared scratch) and compare every result with the
-plan-based hartree_solve_density on the same density, within the tolerances the
-other parity tests use.  This file runs last so that a failure here comes after
-every other test has already run; it also passes on its own in a fresh process.
+These tests call that entry point through the C ABI three times in a row
+(FP32, then FP64, then FP32 again on the shared scratch) and compare every
+result with the FP64 oracle and with the plan-based hartree_solve_density on
+the same density, within the tolerances the other parity tests use.  They also
+check that a call leaves the device's free memory unchanged.  This file runs
+last so that a failure here comes after every other test has already run; it
+also passes on its own in a fresh process.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1209_4506_gb300 import capi, synth
 from paper_1209_4506_gb300.hartree import HartreePlan
 
@@ -95,6 +98,28 @@ def test_noalloc_matches_plan_solve_on_consecutive_calls():
     assert abs(e2.item() - f64.item()) <= TOL["fp64"]["e"] * abs(f64.item())
     # the scratch keeps the previous call's contents; nothing of it leaks into the next result
     assert torch.equal(v3, v1) and e3.item() == e1.item()
+    # and against the FP64 oracle on the same (rounded) densities
+    for v, e, c, rho, prec in ((v1, e1, c32, rho32, "fp32"), (v2, e2, c64, rho64, "fp64")):
+        v_ref, e_ref, _, _ = O.poisson(c, rho.double().cpu().numpy())
+        assert rel_l2(v, torch.tensor(v_ref, device=v.device)) <= TOL[prec]["v"]
+        assert abs(e.item() - e_ref) <= TOL[prec]["e"] * abs(e_ref)
+
+
+def test_noalloc_allocates_no_device_memory():
+    n32, c32, rho32 = fp32_case()
+    vh = torch.empty_like(rho32)
+    eh = torch.empty((), dtype=torch.float64, device=rho32.device)
+    stream = torch.cuda.current_stream().cuda_stream
+    d = desc_for(n32, c32, "fp32")
+    capi.check(capi.hartree_solve_density_noalloc(ctypes.byref(d), rho32.data_ptr(), vh.data_ptr(), eh.data_ptr(),
+                                                  stream))  # warm-up: the per-device set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    capi.check(capi.hartree_solve_density_noalloc(ctypes.byref(d), rho32.data_ptr(), vh.data_ptr(), eh.data_ptr(),
+                                                  stream))
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_noalloc_rejects_grids_beyond_the_scratch():
