@@ -449,14 +449,6 @@ __global__ void __launch_bounds__(NT, MODE == 2 && min_ctas<NT>() > 2 ? min_ctas
     }
 }
 
-// Rows of one tensor-map box along a column of n points: the largest divisor of n
-// within the 256-element box limit.
-__host__ __device__ constexpr int box_rows(int n) {
-    for (int r = n < 256 ? n : 256; r > 1; --r)
-        if (n % r == 0) return r;
-    return 1;
-}
-
 // ------------------------------------------------------------------ TMA-streamed b and a passes (FP32)
 // Persistent CTAs walk the tiles blockIdx.x, blockIdx.x + gridDim.x, ... through
 // a ring of NBUF shared-memory tile buffers.  Thread 0 keeps NBUF - 1 tile
@@ -1014,6 +1006,11 @@ bool col_tma_available(const Plan& p, int axis) {
     return p.prec != HARTREE_FP64 && p.tma_ok && with_col_tma_cfg(p.n[axis], 0, [](auto) {});
 }
 
+// Variants of the b / a passes, in order: the plain kernels (col_variants), the TMA-streamed
+// kernels (col_tma_variants, when available) and the paired-lane TMA kernels of pair_passes.cu.
+int col_tma_count(const Plan& p, int axis) { return col_tma_available(p, axis) ? col_tma_variants(p.n[axis]) : 0; }
+int col_pair_count(const Plan& p, int axis) { return col_pair_available(p, axis) ? col_pair_variants(p.n[axis]) : 0; }
+
 // c-pass configurations by M = N3 / 2 and variant (variant 1: half the lines per CTA).
 template <typename T, class F>
 bool with_line_cfg(int m, int variant, F&& f) {
@@ -1119,6 +1116,7 @@ cudaError_t configure_fast_t(const Plan& p, int optin) {
         for (int ax = 0; ax < 2; ++ax)
             if (col_tma_available(p, ax))
                 for (int v = 0; v < col_tma_variants(p.n[ax]); ++v) with_col_tma_cfg(p.n[ax], v, cfg);
+        if (e == cudaSuccess) e = configure_col_pair(p, optin);
     }
     return e;
 }
@@ -1158,6 +1156,8 @@ long long launch_fast_pass_t(const Plan& p, int pass, const void* rho, void* vh,
     const int axis = (pass == 2) ? 0 : 1;  // transformed axis: a for pass 2, b for passes 1 and 3
     if constexpr (sizeof(T) == 4) {
         const int tv = pass_variant(p, pass) - col_variants(p.n[axis]);
+        const int pv = tv - col_tma_count(p, axis);
+        if (pv >= 0 && col_pair_available(p, axis)) return launch_col_pair(p, pass, pv, a, s);
         if (tv >= 0 && col_tma_available(p, axis)) {
             // TMA-streamed persistent kernel, one CTA per SM
             with_col_tma_cfg(p.n[axis], tv, [&](auto c) {
@@ -1191,7 +1191,7 @@ int single_variants(const Plan& p, int kind) {
                                 : 1;
     const int ax = kind == 1 ? 1 : 0;
     if (!(p.use_fast & (kind == 1 ? 2 : 4))) return 1;
-    return col_variants(p.n[ax]) + (col_tma_available(p, ax) ? col_tma_variants(p.n[ax]) : 0);
+    return col_variants(p.n[ax]) + col_tma_count(p, ax) + col_pair_count(p, ax);
 }
 
 void pair_variants(int V, int v, int* first, int* second) {

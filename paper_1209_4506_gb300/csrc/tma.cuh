@@ -15,6 +15,14 @@ namespace hartree {
 constexpr uint32_t kSpinLimit = 1u << 26;  // try_wait probes before a wait is declared failed
 constexpr int kErrTimeout = 1;             // bit in the plan's device error word
 
+// Rows of one tensor-map box along a column of n points: the largest divisor of n
+// within the 256-element box limit.
+__host__ __device__ constexpr int box_rows(int n) {
+    for (int r = n < 256 ? n : 256; r > 1; --r)
+        if (n % r == 0) return r;
+    return 1;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
