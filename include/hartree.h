@@ -281,6 +281,27 @@ int hartree_solve_batched(hartree_batch batch, const double* pos, const double* 
                           void* stream);
 int hartree_batch_device_status(hartree_batch batch);
 
+/*
+ * Fault injection for the bounded dependency waits of hartree_solve_batched
+ * (the paper has no counterpart; it exists so that the timeout path can be
+ * exercised on a shared GPU without hanging or faulting it).  Off by default.
+ *   skip_stage  -1: off.  0..8: in every later hartree_solve_batched, item 0
+ *               of that stage of cell skip_cell does its work but never counts
+ *               itself done, so the items of the next stage of that cell wait
+ *               for it until their limit runs out, give up, and set the
+ *               batch's error word (hartree_batch_device_status then returns
+ *               HARTREE_ERR_TIMEOUT and that launch's results are incomplete).
+ *               Stages: 0 atom preparation, 1 Gaussian factors, 2 leaf boxes,
+ *               3 splat, 4 c pass, 5 b pass, 6 a pass with Green and E_H,
+ *               7 b inverse, 8 c inverse (9, the E_H sum, has no successor).
+ *   skip_cell   the cell, in [0, n_cells), when skip_stage >= 0
+ *   spin_limit  probes (each about 64 ns apart) a dependency wait makes before
+ *               it gives up; 0 restores the default (2^26, seconds).  A short
+ *               limit keeps an injected timeout to milliseconds.
+ * No device work; HARTREE_ERR_INVALID for a stage or cell out of range.
+ */
+int hartree_batch_fault_inject(hartree_batch batch, int skip_stage, int skip_cell, unsigned spin_limit);
+
 /* ---------------------------------------------------------------- no device allocation */
 
 /*

@@ -51,6 +51,7 @@ EXPORTED = (
     "hartree_batch_offsets",
     "hartree_solve_batched",
     "hartree_batch_device_status",
+    "hartree_batch_fault_inject",
     "hartree_status_string",
     "hartree_last_error",
 )
@@ -116,6 +117,7 @@ def lib():
             L.hartree_batch_offsets.argtypes = [_vp, _vp, _vp]
             L.hartree_solve_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
             L.hartree_batch_device_status.argtypes = [_vp]
+            L.hartree_batch_fault_inject.argtypes = [_vp, _i, _i, ctypes.c_uint]
             L.hartree_status_string.argtypes = [_i]
             L.hartree_status_string.restype = ctypes.c_char_p
             L.hartree_last_error.argtypes = []
@@ -161,3 +163,4 @@ hartree_batch_destroy = _call("hartree_batch_destroy")
 hartree_batch_offsets = _call("hartree_batch_offsets")
 hartree_solve_batched = _call("hartree_solve_batched")
 hartree_batch_device_status = _call("hartree_batch_device_status")
+hartree_batch_fault_inject = _call("hartree_batch_fault_inject")

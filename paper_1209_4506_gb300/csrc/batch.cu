@@ -42,6 +42,10 @@ struct BatchArgs {
     unsigned long long* head;  // next item (zeroed before the launch)
     int* done;                 // [NST][n_cells] finished items (zeroed before the launch)
     int* err;
+    // fault injection (tests of the bounded waits; off: skip_stage = -1, spin_limit = kSpinLimit):
+    // item 0 of (skip_stage, skip_cell) does its work but is never counted done
+    int skip_stage, skip_cell;
+    uint32_t spin_limit;  // dependency-wait probes before a wait gives up
 };
 
 __global__ void __launch_bounds__(kThreads) k_batched(BatchArgs b, const double* pos, const double* q, float* vh,
@@ -78,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchArgs b, const double*
                 volatile int* d = b.done + (s - 1) * b.n_cells + c;
                 uint32_t it = 0;
                 while (*d < need) {
-                    if (++it > kSpinLimit) {
+                    if (++it > b.spin_limit) {
                         atomicOr(b.err, kErrTimeout);
                         ok = 0;
                         break;
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchArgs b, const double*
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !(s == b.skip_stage && c == b.skip_cell && t == 0)) {
             __threadfence();
             atomicAdd(b.done + s * b.n_cells + c, 1);
         }
@@ -146,6 +150,8 @@ struct BatchHost {
     size_t smem = 0;
     int grid = 0;
     int n_cells = 0;
+    int skip_stage = -1, skip_cell = 0;  // fault injection (hartree_batch_fault_inject)
+    uint32_t spin_limit = kSpinLimit;
 };
 
 }  // namespace hartree
@@ -302,10 +308,24 @@ extern "C" int hartree_solve_batched(hartree_batch batch, const double* pos, con
         a.head = h.head_d;
         a.done = h.done_d;
         a.err = h.err_d;
+        a.skip_stage = h.skip_stage;
+        a.skip_cell = h.skip_cell;
+        a.spin_limit = h.spin_limit;
         k_batched<<<h.grid, kThreads, h.smem, s>>>(a, pos, q, static_cast<float*>(vh), eh);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return batch_fail(HARTREE_ERR_CUDA, cudaGetErrorString(e));
+    return HARTREE_OK;
+}
+
+extern "C" int hartree_batch_fault_inject(hartree_batch batch, int skip_stage, int skip_cell, unsigned spin_limit) {
+    if (!batch) return batch_fail(HARTREE_ERR_INVALID, "batch_fault_inject: null batch");
+    BatchHost& h = batch->h;
+    if (skip_stage < -1 || skip_stage >= NST - 1 || (skip_stage >= 0 && (skip_cell < 0 || skip_cell >= h.n_cells)))
+        return batch_fail(HARTREE_ERR_INVALID, "batch_fault_inject: stage must be in [-1, 8], cell in [0, n_cells)");
+    h.skip_stage = skip_stage;
+    h.skip_cell = skip_stage >= 0 ? skip_cell : 0;
+    h.spin_limit = spin_limit > 0 ? (uint32_t)spin_limit : kSpinLimit;
     return HARTREE_OK;
 }
 

@@ -310,3 +310,8 @@ class HartreeBatch:
 
     def device_status(self):
         capi.check(capi.hartree_batch_device_status(self.handle))
+
+    def fault_inject(self, skip_stage: int = -1, skip_cell: int = 0, spin_limit: int = 0):
+        """Test hook: item 0 of (skip_stage, skip_cell) never reports done, and dependency waits give up
+        after spin_limit probes (0: the default).  skip_stage = -1 switches it off."""
+        capi.check(capi.hartree_batch_fault_inject(self.handle, int(skip_stage), int(skip_cell), int(spin_limit)))

@@ -123,3 +123,34 @@ def test_cuda_graph_capture_and_replay():
     v_ref, e_ref = B.solve(pos, q)
     torch.cuda.synchronize()
     assert torch.equal(vh, v_ref) and torch.equal(eh, e_ref)
+
+
+def test_injected_lost_producer_times_out_and_the_next_solve_is_correct():
+    """Failure detection without a GPU fault: one producer item (stage 4, the c pass, of cell 1)
+    is told never to report itself done, and the dependency waits get a short limit.  The
+    items of the next stage of that cell wait, give up and set the batch's error word; the
+    host reads HARTREE_ERR_TIMEOUT.  The context stays usable: with the injection switched
+    off, the next solve on the same batch matches the oracle."""
+    from paper_1209_4506_gb300 import capi
+
+    O.set_threads(os.cpu_count() or 1)
+    cells = sorted(synth.config4(), key=lambda S: np.prod(S.n))[:3]
+    B, pos, q = make_batch(cells)
+    with pytest.raises(capi.HartreeError):
+        B.fault_inject(skip_stage=9, skip_cell=0)  # the E_H sum has no successor: refused
+    with pytest.raises(capi.HartreeError):
+        B.fault_inject(skip_stage=4, skip_cell=len(cells))
+    B.fault_inject(skip_stage=4, skip_cell=1, spin_limit=2000)  # about 0.1 ms per wait
+    vh, eh = B.solve(pos, q)
+    with pytest.raises(capi.HartreeError) as ei:
+        B.device_status()
+    assert ei.value.status == capi.HARTREE_ERR_TIMEOUT
+    B.device_status()  # the error word was cleared by the check
+    B.fault_inject(-1)
+    vh, eh = B.solve(pos, q)
+    B.device_status()
+    for c, S in enumerate(cells):
+        ref = O.solve_system(S, with_forces=False)
+        v = B.cell_view(vh, c).cpu().numpy().astype(np.float64)
+        assert rel_l2(v, ref["vh"]) <= TOL_V, S.name
+        assert abs(eh[c].item() - ref["eh"]) <= TOL_E * abs(ref["eh"]), S.name
