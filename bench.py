@@ -304,6 +304,42 @@ def adjoint_section(plan, pos, q, rho, vh, stream, reps, plain_solve_ms):
                     "(or keeping it); E_H(rho) -> V_H dV (backward = one more solve)"}
 
 
+def other_grids_section(dev, stream, reps):
+    """The grids that are not powers of two: 360 x 384 x 400 (orthorhombic cell at diamond density) and the
+    paper's 420 x 420 x 210 (16,384 diamond atoms).  Per grid: the autotuned solve (five passes and the E_H
+    reduction, CUDA events) with its fraction of the measured HBM peak on the 40 N_tot yardstick, and the whole
+    step (setup, splat, solve, forces) over the bisection-ordered atoms."""
+    import torch
+
+    from paper_1209_4506_gb300 import synth
+    from paper_1209_4506_gb300.hartree import HartreePlan, atoms_reorder
+
+    pk, _ = peaks()
+    out = {}
+    for key, S in (("ortho360", synth.config3b()), ("paper420", synth.config_paper420())):
+        apl = 16
+        perm, _ = atoms_reorder(S.pos, (S.n_atoms + apl - 1) // apl)
+        plan = HartreePlan(S.n, S.cell, S.sigma, "fp32", atoms_per_leaf=apl, max_atoms=S.n_atoms)
+        variants = plan.autotune()
+        pos = torch.tensor(S.pos[perm], device=dev)
+        q = torch.tensor(S.q[perm], device=dev)
+        rho = plan.splat(pos, q)
+        vh = torch.empty_like(rho)
+        eh = torch.empty((), dtype=torch.float64, device=dev)
+        f = torch.empty((S.n_atoms, 3), dtype=torch.float64, device=dev)
+        t_solve = time_events(lambda: plan.solve_density(rho, vh, eh), reps, stream)
+        t_step = time_events(lambda: plan.step(pos, q, vh=vh, eh=eh, f=f), reps, stream)
+        plan.device_status()
+        y = 40.0 * S.n_tot
+        out[key] = {"grid": list(S.n), "atoms": S.n_atoms, "solve_ms": t_solve,
+                    "solve_gbs": y / (t_solve * 1e-3) / 1e9,
+                    "solve_frac": y / (t_solve * 1e-3) / 1e9 / pk["hbm_gbs"],
+                    "step_ms": t_step, "variants": variants,
+                    "note": "solve = five passes + E_H reduction; frac of the measured HBM peak, 40 N_tot bytes"}
+        plan.close()
+    return out
+
+
 def side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrier, ybytes, plain_solve_ms, dev):
     """e2e through the C ABI with host buffers, the adjoint forms and the batched form."""
     import torch
@@ -325,7 +361,8 @@ def side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrie
     side_reps = max(5, min(args.steps, 50))
     adjoint = adjoint_section(plan, pos, q, rho, vh, stream, side_reps, plain_solve_ms)
     batched = batched_section(dev, stream, side_reps)
-    return e2e, adjoint, batched
+    other = other_grids_section(dev, stream, side_reps)
+    return e2e, adjoint, batched, other
 
 
 def main():
@@ -451,9 +488,9 @@ def main():
                       "unit": "GB/s", "frac": ybytes / (solve_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                       "note": "five Poisson passes, 40 N_tot algorithmic bytes"}
 
-    e2e = adjoint = batched = None
+    e2e = adjoint = batched = other = None
     if not args.skip_side:
-        e2e, adjoint, batched = side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrier, ybytes,
+        e2e, adjoint, batched, other = side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrier, ybytes,
                                               solve_ms + kernels_ms["splat"], dev)
 
     cpu = None
@@ -482,7 +519,10 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "solve_ms": solve_ms, "solve_gbs": ybytes / (solve_ms * 1e-3) / 1e9,
             "solve_points_per_s": ntot / (solve_ms * 1e-3), "solve_roofline": solve_roofline,
-            "kernels_ms": kernels_ms, "batched": batched, "adjoint": adjoint, "reorder_ms": reorder_ms,
+            "kernels_ms": kernels_ms, "batched": batched, "adjoint": adjoint, "other_grids": other,
+            "solve_ms_ortho360": other["ortho360"]["solve_ms"] if other else None,
+            "solve_ms_paper420": other["paper420"]["solve_ms"] if other else None,
+            "reorder_ms": reorder_ms,
             "eh": float(eh.item()),
         }
         print(json.dumps(line), flush=True)
