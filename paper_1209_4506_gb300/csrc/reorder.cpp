@@ -20,50 +20,9 @@
 #include <vector>
 
 #include "../../include/hartree.h"
+#include "sym3.h"
 
 namespace {
-
-// Eigen-decomposition of a symmetric 3x3 matrix S (row major) by Jacobi
-// rotations with the tau-form update; columns of E are the eigenvectors.
-void sym3_eigen(double S[3][3], double lam[3], double E[3][3]) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) E[i][j] = (i == j) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 50; ++sweep) {
-        const double off = std::fabs(S[0][1]) + std::fabs(S[0][2]) + std::fabs(S[1][2]);
-        if (off == 0.0) break;
-        const double diag = std::fabs(S[0][0]) + std::fabs(S[1][1]) + std::fabs(S[2][2]);
-        if (off < 1e-18 * diag) break;
-        static const int P[3] = {0, 0, 1}, Q[3] = {1, 2, 2};
-        for (int pq = 0; pq < 3; ++pq) {
-            const int p = P[pq], q = Q[pq];
-            const double spq = S[p][q];
-            if (spq == 0.0) continue;
-            const double h = S[q][q] - S[p][p];
-            double t;
-            if (std::fabs(spq) < 1e-300 * std::fabs(h)) {
-                t = spq / h;
-            } else {
-                const double th = 0.5 * h / spq;
-                t = 1.0 / (std::fabs(th) + std::sqrt(1.0 + th * th));
-                if (th < 0.0) t = -t;
-            }
-            const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c, tau = s / (1.0 + c);
-            S[p][p] -= t * spq;
-            S[q][q] += t * spq;
-            S[p][q] = S[q][p] = 0.0;
-            const int r = 3 - p - q;  // the remaining index
-            const double srp = S[r][p], srq = S[r][q];
-            S[r][p] = S[p][r] = srp - s * (srq + tau * srp);
-            S[r][q] = S[q][r] = srq + s * (srp - tau * srq);
-            for (int k = 0; k < 3; ++k) {
-                const double ekp = E[k][p], ekq = E[k][q];
-                E[k][p] = ekp - s * (ekq + tau * ekp);
-                E[k][q] = ekq + s * (ekp - tau * ekq);
-            }
-        }
-    }
-    for (int i = 0; i < 3; ++i) lam[i] = S[i][i];
-}
 
 struct Node {
     int begin, count, procs;
@@ -109,20 +68,8 @@ extern "C" int hartree_atoms_reorder(const double* pos, const double* w, int n, 
         Mx[1][0] = Mx[0][1];
         Mx[2][0] = Mx[0][2];
         Mx[2][1] = Mx[1][2];
-        double lam[3], E[3][3];
-        sym3_eigen(Mx, lam, E);
-        int top = 0;
-        for (int e = 1; e < 3; ++e)
-            if (lam[e] > lam[top]) top = e;
-        double ax[3] = {E[0][top], E[1][top], E[2][top]};
-        const double nrm = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
-        int big = 0;
-        for (int d = 0; d < 3; ++d) {
-            ax[d] /= nrm;
-            if (std::fabs(ax[d]) > std::fabs(ax[big])) big = d;
-        }
-        if (ax[big] < 0.0)
-            for (double& v : ax) v = -v;
+        double ax[3];
+        hartree::principal_axis(Mx, ax);
         key.resize(nd.count);
         for (int a = 0; a < nd.count; ++a) {
             const int i = ids[a];
