@@ -10,15 +10,22 @@
 // 16-point complex DFT of a batch of rows is the real product
 //   [Re x | Im x] (rows x 32) . M (32 x 32),
 // M holding cos and +-sin of 2 pi n k / 16.  FP32 values are split into
-// 16-bit pairs x = x_h + x_l (x_l = round(x - x_h)), likewise M = M_h + M_l in
-// FP64 on the host, and the MMA computes x_h M_h + x_h M_l + x_l M_h with FP32
-// accumulation as one K = 96 product [x_h | x_h | x_l] . [M_h ; M_l ; M_h].
-// With p significant bits per part the dropped x_l M_l term and the split
-// residual are about 2^-2p relative per product: 2^-22 for FP16 (p = 11, the
-// default) and 2^-16 for BF16 (p = 8; four such stages per solve exceed a
-// 1e-5 bar on V_H).  FP16 needs range: each row of 16 complex inputs is scaled
-// by a power of two that puts its largest magnitude in [2^14, 2^15), which is
-// exact, and the same thread divides its output row by it.
+// 16-bit parts and the MMA accumulates, in FP32, the products of the parts
+// whose order is low enough for an FP32 result:
+//   FP16 (the default, p = 11 significant bits per part): x = x_h + x_l,
+//     M = M_h + M_l (the table split in FP64 on the host), and
+//     x_h M_h + x_h M_l + x_l M_h as one K = 96 product
+//     [x_h | x_h | x_l] . [M_h ; M_l ; M_h]; the dropped x_l M_l term and the
+//     split residual are about 2^-22 relative per product.  FP16 needs range:
+//     each row of 16 complex inputs is scaled by a power of two that puts its
+//     largest magnitude in [2^14, 2^15), which is exact, and the same thread
+//     divides its output row by it.
+//   BF16 (p = 8, the FP32 exponent range, no scaling): two parts would leave
+//     2^-16 per product, and four such stages per solve exceed the 1e-5 bar on
+//     V_H, so x = x0 + x1 + x2 and M = M0 + M1 + M2 (24 bits each) and the six
+//     products of order <= 2, x0 M0 + x1 M0 + x0 M1 + x2 M0 + x1 M1 + x0 M2, form
+//     one K = 192 product [x0 | x1 | x0 | x2 | x1 | x0] . [M0 ; M0 ; M1 ; M0 ; M1 ; M2];
+//     the dropped terms are about 2^-24 relative.
 //
 // One CTA of 128 threads transforms 8 complex columns (128 rows of 16-point
 // DFTs per stage, one M = 128 MMA tile of N = 32, accumulator in 32 TMEM
@@ -40,11 +47,16 @@ namespace {
 
 constexpr int kTcCols = 8;                  // complex columns per CTA
 constexpr int kTcThreads = 128;             // one thread per row of the MMA tile
-constexpr int kTcK = 96;                    // [x_h | x_h | x_l]
+constexpr int kTcKMax = 192;                // the longest contraction (BF16: six segments of 32)
 constexpr int kX2Stride = 274;              // c stride of the transposed stage-A output (conflict-free)
 constexpr int kX2Row = 17;                  // k1 stride
 constexpr uint32_t kTcLbo = 128;            // core matrices along K
-constexpr uint32_t kTcSbo = kTcK / 8 * 128;  // core matrices along rows
+
+// K of the split product: 32 values (Re, Im of 16 inputs) per segment, 3 segments (FP16) or 6 (BF16).
+template <bool F16>
+__host__ __device__ constexpr int tc_k() {
+    return F16 ? 96 : 192;
+}
 
 struct TcArgs {
     cpx<float>* W;
@@ -54,11 +66,14 @@ struct TcArgs {
     int* err;
 };
 
+// Shared memory of one CTA for a contraction of length K (sized per operand format, so the
+// FP16 split keeps its occupancy).
+template <int K>
 struct TcSmem {
     cpx<float> X[256 * kTcCols];         // input columns: X[n][c]
     cpx<float> X2[kTcCols * kX2Stride];  // stage-A output: X2[c][k1][n2]
-    uint16_t A[kTcThreads * kTcK];
-    uint16_t B[32 * kTcK];
+    uint16_t A[kTcThreads * K];
+    uint16_t B[32 * K];
     uint64_t bar;
     uint32_t tbase;
 };
@@ -79,10 +94,12 @@ __device__ __forceinline__ float from16(uint16_t x) {
         return __bfloat162float(__ushort_as_bfloat16(x));
 }
 
-// Row r of the A operand from 16 complex values: K = [re_h(16) im_h(16) | re_h im_h | re_l im_l].
-// FP16 rows are scaled by a power of two first; returns the factor that undoes it.
+// Row r of the A operand from 16 complex values, segments of 32 (re(16), im(16)): FP16 [h | h | l],
+// BF16 [x0 | x1 | x0 | x2 | x1 | x0].  FP16 rows are scaled by a power of two first; returns the
+// factor that undoes it.
 template <bool F16>
 __device__ __forceinline__ float build_row(uint16_t* A, int r, float* re, float* im) {
+    constexpr int K = tc_k<F16>();
     float undo = 1.f;
     if constexpr (F16) {
         float m = 0.f;
@@ -96,43 +113,54 @@ __device__ __forceinline__ float build_row(uint16_t* A, int r, float* re, float*
             for (int n = 0; n < 16; ++n) re[n] *= sc, im[n] *= sc;
         }
     }
-    uint16_t h[32], l[32];
+    // parts: x = p[0] + p[1] (+ p[2]), each rounded from the remainder of the previous ones
+    constexpr int NP = F16 ? 2 : 3;
+    uint16_t part[NP][32];
 #pragma unroll
-    for (int n = 0; n < 16; ++n) {
-        h[n] = to16<F16>(re[n]);
-        h[16 + n] = to16<F16>(im[n]);
-        l[n] = to16<F16>(re[n] - from16<F16>(h[n]));
-        l[16 + n] = to16<F16>(im[n] - from16<F16>(h[16 + n]));
+    for (int n = 0; n < 32; ++n) {
+        float rem = n < 16 ? re[n] : im[n - 16];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            part[q][n] = to16<F16>(rem);
+            rem -= from16<F16>(part[q][n]);
+        }
     }
+    // segment order: FP16 h, h, l; BF16 x0, x1, x0, x2, x1, x0
+    constexpr int seg16[3] = {0, 0, 1};
+    constexpr int segbf[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {  // 16-byte chunks of 8 K values
-        const uint16_t* src = j < 8 ? h + (j & 3) * 8 : l + (j - 8) * 8;
+    for (int j = 0; j < K / 8; ++j) {  // 16-byte chunks of 8 K values
+        const int sg = F16 ? seg16[j / 4] : segbf[j / 4];
+        const uint16_t* src = part[sg] + (j & 3) * 8;
         uint4 v;
         v.x = (uint32_t)src[0] | ((uint32_t)src[1] << 16);
         v.y = (uint32_t)src[2] | ((uint32_t)src[3] << 16);
         v.z = (uint32_t)src[4] | ((uint32_t)src[5] << 16);
         v.w = (uint32_t)src[6] | ((uint32_t)src[7] << 16);
-        *reinterpret_cast<uint4*>(A + kmajor_index(r, 8 * j, kTcK)) = v;
+        *reinterpret_cast<uint4*>(A + kmajor_index(r, 8 * j, K)) = v;
     }
     return undo;
 }
 
-// Six K = 16 MMAs of the 128 x 32 x 96 product into TMEM, committed to `bar`.
+// The K = 16 MMAs of the 128 x 32 x K product into TMEM (6 for FP16, 12 for BF16), committed to `bar`.
 template <bool F16>
-__device__ __forceinline__ void issue_dft(TcSmem& s, uint32_t tmem) {
+__device__ __forceinline__ void issue_dft(TcSmem<tc_k<F16>()>& s, uint32_t tmem) {
+    constexpr int K = tc_k<F16>();
+    constexpr uint32_t sbo = K / 8 * 128;  // core matrices along rows
     tc_fence_after();
     const uint32_t idesc = F16 ? idesc_f16_f32(128, 32) : idesc_bf16_f32(128, 32);
 #pragma unroll
-    for (int ks = 0; ks < kTcK / 16; ++ks)
-        umma_f16(tmem, smem_desc(s.A + kmajor_index(0, 16 * ks, kTcK), kTcLbo, kTcSbo),
-                  smem_desc(s.B + kmajor_index(0, 16 * ks, kTcK), kTcLbo, kTcSbo), idesc, ks > 0 ? 1u : 0u);
+    for (int ks = 0; ks < K / 16; ++ks)
+        umma_f16(tmem, smem_desc(s.A + kmajor_index(0, 16 * ks, K), kTcLbo, sbo),
+                  smem_desc(s.B + kmajor_index(0, 16 * ks, K), kTcLbo, sbo), idesc, ks > 0 ? 1u : 0u);
     umma_commit(&s.bar);
 }
 
 template <bool INV, bool F16>
 __global__ void __launch_bounds__(kTcThreads) k_col_tc(TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
-    TcSmem& s = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    TcSmem<tc_k<F16>()>& s =
+        *reinterpret_cast<TcSmem<tc_k<F16>()>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ia = blockIdx.x / a.chunks;
     const int c0 = (blockIdx.x - ia * a.chunks) * kTcCols;
@@ -152,9 +180,11 @@ __global__ void __launch_bounds__(kTcThreads) k_col_tc(TcArgs a) {
         s.X[e] = c < nc ? col[(long long)n * a.ldc + c] : mk(0.f, 0.f);
     }
     {
-        const uint4* src = reinterpret_cast<const uint4*>(a.dft + (INV ? 32 * kTcK : 0));  // F16 and BF16 tables differ: the host passes the right one
+        // the host uploads the table of the plan's operand format: [forward, inverse], 32 x K each
+        constexpr int K = tc_k<F16>();
+        const uint4* src = reinterpret_cast<const uint4*>(a.dft + (INV ? 32 * K : 0));
         uint4* dst = reinterpret_cast<uint4*>(s.B);
-        for (int e = tid; e < 32 * kTcK / 8; e += kTcThreads) dst[e] = src[e];
+        for (int e = tid; e < 32 * K / 8; e += kTcThreads) dst[e] = src[e];
     }
     __syncthreads();
 
@@ -233,25 +263,27 @@ __global__ void __launch_bounds__(kTcThreads) k_col_tc(TcArgs a) {
 
 bool tc_split_supported(const Plan& p) { return p.n[1] == 256; }
 
-size_t tc_smem() { return sizeof(TcSmem) + 1024; }
+size_t tc_smem(bool f16) {
+    return (f16 ? sizeof(TcSmem<tc_k<true>()>) : sizeof(TcSmem<tc_k<false>()>)) + 1024;
+}
 
 cudaError_t configure_tc_kernels(const Plan& p) {
     if (p.prec != HARTREE_FP32_TC_SPLIT) return cudaSuccess;
-    const int sm = (int)tc_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_col_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const int s16 = (int)tc_smem(true), sbf = (int)tc_smem(false);
+    cudaError_t e = cudaFuncSetAttribute(k_col_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s16);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s16);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_col_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        e = cudaFuncSetAttribute(k_col_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbf);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbf);
     return e;
 }
 
-size_t tc_table_bytes() { return 2 * 32 * kTcK * sizeof(uint16_t); }
+size_t tc_table_bytes() { return 2 * 32 * kTcKMax * sizeof(uint16_t); }
 
-// Operand B of the 16-point DFT for both directions, split into BF16 high and
-// low parts in FP64, laid out K-major: row j < 16 is Re X_j, row 16 + j is Im X_j;
-// column q < 16 multiplies Re x_q, 16 + q multiplies Im x_q; columns 0..31 hold
-// the high parts, 32..63 the low parts, 64..95 the high parts again.
+// Operand B of the 16-point DFT for both directions, split into 16-bit parts in
+// FP64, laid out K-major: row j < 16 is Re X_j, row 16 + j is Im X_j; within a
+// segment of 32 columns, column q < 16 multiplies Re x_q, 16 + q multiplies Im x_q.
+// Segments: FP16 M_h, M_l, M_h; BF16 M0, M0, M1, M0, M1, M2 (matching the A rows).
 static uint16_t host16(double x, bool f16) {
     return f16 ? __half_as_ushort(__float2half_rn((float)x)) : __bfloat16_as_ushort(__float2bfloat16_rn((float)x));
 }
@@ -259,11 +291,13 @@ static double host_back(uint16_t x, bool f16) {
     return f16 ? (double)__half2float(__ushort_as_half(x)) : (double)__bfloat162float(__ushort_as_bfloat16(x));
 }
 
-static void tc_dft_tables(uint16_t* out /* [2][32 * 96] */, bool f16) {
+static void tc_dft_tables(uint16_t* out /* [2][32 * K] */, bool f16) {
     const double pi = 3.14159265358979323846;
+    const int K = f16 ? tc_k<true>() : tc_k<false>();
+    static const int seg16[3] = {0, 1, 0}, segbf[6] = {0, 0, 1, 0, 1, 2};
     for (int dir = 0; dir < 2; ++dir) {
         const double sg = dir == 0 ? -1.0 : 1.0;  // exp(sg 2 pi i n k / 16)
-        uint16_t* B = out + dir * 32 * kTcK;
+        uint16_t* B = out + dir * 32 * K;
         for (int j = 0; j < 32; ++j)
             for (int q = 0; q < 32; ++q) {
                 const int k = j & 15, n = q & 15;
@@ -275,18 +309,21 @@ static void tc_dft_tables(uint16_t* out /* [2][32 * 96] */, bool f16) {
                     m = q < 16 ? c : -sn;
                 else
                     m = q < 16 ? sn : c;
-                const uint16_t h = host16(m, f16);
-                const uint16_t l = host16(m - host_back(h, f16), f16);
-                B[kmajor_index(j, q, kTcK)] = h;
-                B[kmajor_index(j, 32 + q, kTcK)] = l;
-                B[kmajor_index(j, 64 + q, kTcK)] = h;
+                uint16_t part[3];
+                double rem = m;
+                for (int pq = 0; pq < 3; ++pq) {
+                    part[pq] = host16(rem, f16);
+                    rem -= host_back(part[pq], f16);
+                }
+                for (int sgi = 0; sgi < K / 32; ++sgi)
+                    B[kmajor_index(j, 32 * sgi + q, K)] = part[f16 ? seg16[sgi] : segbf[sgi]];
             }
     }
 }
 
 cudaError_t upload_tc_tables(const Plan& p) {
     if (p.prec != HARTREE_FP32_TC_SPLIT) return cudaSuccess;
-    std::vector<uint16_t> t(2 * 32 * kTcK);
+    std::vector<uint16_t> t(2 * 32 * kTcKMax);
     tc_dft_tables(t.data(), !(p.desc.flags & HARTREE_FLAG_TC_BF16));
     return cudaMemcpy(p.tc_dft, t.data(), tc_table_bytes(), cudaMemcpyHostToDevice);
 }
@@ -304,16 +341,17 @@ long long launch_tc_pass(const Plan& p, int pass, cudaStream_t s) {
     a.err = p.d_err;
     const unsigned grid = (unsigned)(p.n[0] * a.chunks);
     const bool f16 = !(p.desc.flags & HARTREE_FLAG_TC_BF16);
+    const size_t sm = tc_smem(f16);
     if (pass == 1) {
         if (f16)
-            k_col_tc<false, true><<<grid, kTcThreads, tc_smem(), s>>>(a);
+            k_col_tc<false, true><<<grid, kTcThreads, sm, s>>>(a);
         else
-            k_col_tc<false, false><<<grid, kTcThreads, tc_smem(), s>>>(a);
+            k_col_tc<false, false><<<grid, kTcThreads, sm, s>>>(a);
     } else {
         if (f16)
-            k_col_tc<true, true><<<grid, kTcThreads, tc_smem(), s>>>(a);
+            k_col_tc<true, true><<<grid, kTcThreads, sm, s>>>(a);
         else
-            k_col_tc<true, false><<<grid, kTcThreads, tc_smem(), s>>>(a);
+            k_col_tc<true, false><<<grid, kTcThreads, sm, s>>>(a);
     }
     return grid;
 }
