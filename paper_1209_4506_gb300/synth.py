@@ -174,6 +174,28 @@ def config_paper420(seed: Optional[int] = None) -> System:
     return System("diamond-16x16x8 420x420x210 fp32", (420, 420, 210), cell, 0.8, pos, q, "fp32")
 
 
+def config_paper420cube(seed: Optional[int] = None) -> System:
+    """16x16x16 diamond supercell (32,768 atoms, a 107.84 Bohr cube) on 420^3: the paper's
+    32,768-atom memory benchmark grid (Sec. 5.2.6) at its spacing of about 0.257 Bohr.  sigma = 0.8
+    Bohr as on the 420 x 420 x 210 grid.  FP32."""
+    rng = rng_for(7, seed)
+    cell = (16 * DIAMOND_A,) * 3
+    pos = jitter(rng, diamond_supercell((16, 16, 16)), 0.1, cell)
+    q = centred_uniform_charges(rng, pos.shape[0])
+    return System("diamond-16x16x16 420^3 fp32", (420, 420, 420), cell, 0.8, pos, q, "fp32")
+
+
+def config_paper840(seed: Optional[int] = None) -> System:
+    """32x16x16 diamond supercell (65,536 atoms, 215.68 x 107.84 x 107.84 Bohr) on 840 x 420 x 420: the
+    paper's 65,536-atom memory benchmark grid (Sec. 5.2.6) at about 0.257 Bohr.  sigma = 0.8 Bohr.
+    FP32."""
+    rng = rng_for(8, seed)
+    cell = (32 * DIAMOND_A, 16 * DIAMOND_A, 16 * DIAMOND_A)
+    pos = jitter(rng, diamond_supercell((32, 16, 16)), 0.1, cell)
+    q = centred_uniform_charges(rng, pos.shape[0])
+    return System("diamond-32x16x16 840x420x420 fp32", (840, 420, 420), cell, 0.8, pos, q, "fp32")
+
+
 def config4(seed: Optional[int] = None, n_cells: int = 64) -> List[System]:
     """64 independent orthorhombic cells, edges U(8, 30) Bohr, 0.17 Bohr spacing, 8..1000 atoms."""
     rng = rng_for(4, seed)
