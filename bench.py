@@ -44,13 +44,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="diamond512", choices=["diamond512", "diamond256", "ortho360", "paper420"],
+    ap.add_argument("--workload", default="diamond512",
+                    choices=["diamond512", "diamond256", "ortho360", "paper420", "paper420cube", "paper840"],
                     help="diamond256: the 4x4x4 cell on 256^3 (same density and sigma), for small profiler captures; "
                          "ortho360: the 37.9 x 40.4 x 42.1 Bohr cell on 360 x 384 x 400 (diamond density); "
-                         "paper420: 16,384 diamond atoms on the 420 x 420 x 210 grid of the paper's benchmarks")
+                         "paper420: 16,384 diamond atoms on the 420 x 420 x 210 grid of the paper's benchmarks; "
+                         "paper420cube / paper840: 32,768 / 65,536 atoms on 420^3 / 840 x 420 x 420")
     ap.add_argument("--skip-side", action="store_true", help="skip the e2e, adjoint and batched measurements")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16split"],
                     help="bf16split: b passes on the tensor cores (N2 = 256: the diamond256 workload)")
+    ap.add_argument("--tc-parts", default="fp16", choices=["fp16", "bf16"],
+                    help="operand format of the tensor-core split: FP16 hi/lo pairs or BF16 in three parts")
     return ap.parse_args()
 
 
@@ -306,7 +310,8 @@ def adjoint_section(plan, pos, q, rho, vh, stream, reps, plain_solve_ms):
 
 def other_grids_section(dev, stream, reps):
     """The grids that are not powers of two: 360 x 384 x 400 (orthorhombic cell at diamond density) and the
-    paper's 420 x 420 x 210 (16,384 diamond atoms).  Per grid: the autotuned solve (five passes and the E_H
+    paper's memory-benchmark grids at 0.257 Bohr: 420 x 420 x 210, 420^3 and 840 x 420 x 420 (16,384, 32,768 and
+    65,536 diamond atoms).  Per grid: the autotuned solve (five passes and the E_H
     reduction, CUDA events) with its fraction of the measured HBM peak on the 40 N_tot yardstick, and the whole
     step (setup, splat, solve, forces) over the bisection-ordered atoms."""
     import torch
@@ -316,7 +321,8 @@ def other_grids_section(dev, stream, reps):
 
     pk, _ = peaks()
     out = {}
-    for key, S in (("ortho360", synth.config3b()), ("paper420", synth.config_paper420())):
+    for key, S in (("ortho360", synth.config3b()), ("paper420", synth.config_paper420()),
+                   ("paper420cube", synth.config_paper420cube()), ("paper840", synth.config_paper840())):
         apl = 16
         perm, _ = atoms_reorder(S.pos, (S.n_atoms + apl - 1) // apl)
         plan = HartreePlan(S.n, S.cell, S.sigma, "fp32", atoms_per_leaf=apl, max_atoms=S.n_atoms)
@@ -396,6 +402,14 @@ def main():
         S = synth.config_paper420()
         wl_text = ("diamond 16x16x8 supercell, 16384 Gaussian charges (sigma 0.8 Bohr, cutoff 5 sigma), "
                    "420 x 420 x 210 grid (h = 0.257 Bohr)")
+    elif args.workload == "paper420cube":
+        S = synth.config_paper420cube()
+        wl_text = ("diamond 16x16x16 supercell, 32768 Gaussian charges (sigma 0.8 Bohr, cutoff 5 sigma), "
+                   "420^3 grid (h = 0.257 Bohr)")
+    elif args.workload == "paper840":
+        S = synth.config_paper840()
+        wl_text = ("diamond 32x16x16 supercell, 65536 Gaussian charges (sigma 0.8 Bohr, cutoff 5 sigma), "
+                   "840 x 420 x 420 grid (h = 0.257 Bohr)")
     elif args.workload == "ortho360":
         S = synth.config3b()
         wl_text = (f"orthorhombic 37.9 x 40.4 x 42.1 Bohr cell, {S.n_atoms} Gaussian charges at diamond density "
@@ -408,10 +422,26 @@ def main():
     perm, _ = atoms_reorder(S.pos, (S.n_atoms + apl - 1) // apl)
     reorder_ms = 1e3 * (time.perf_counter() - t0)
     pos_h, q_h = S.pos[perm], S.q[perm]
-    plan = HartreePlan(S.n, S.cell, S.sigma, args.precision, atoms_per_leaf=apl, max_atoms=S.n_atoms)
+    from paper_1209_4506_gb300 import capi
+
+    flags = capi.HARTREE_FLAG_TC_BF16 if args.precision == "bf16split" and args.tc_parts == "bf16" else 0
+    plan = HartreePlan(S.n, S.cell, S.sigma, args.precision, atoms_per_leaf=apl, max_atoms=S.n_atoms, flags=flags)
     variants = plan.autotune()
     pos = torch.tensor(pos_h, device=dev)
     q = torch.tensor(q_h, device=dev)
+    # the same decomposition on the device (hartree_atoms_reorder_device), timed with CUDA events
+    pos_raw = torch.tensor(S.pos, device=dev)
+    perm_d = torch.empty(S.n_atoms, dtype=torch.int32, device=dev)
+    ls_d = torch.empty((S.n_atoms + apl - 1) // apl + 1, dtype=torch.int32, device=dev)
+    stream0 = torch.cuda.current_stream(dev)
+
+    def reorder_device():
+        capi.check(capi.hartree_atoms_reorder_device(plan.handle, pos_raw.data_ptr(), None, S.n_atoms,
+                                                     (S.n_atoms + apl - 1) // apl, perm_d.data_ptr(),
+                                                     ls_d.data_ptr(), stream0.cuda_stream))
+
+    reorder_device_ms = time_events(reorder_device, 10, stream0)
+    reorder_device_equal = bool(np.array_equal(perm_d.cpu().numpy(), perm))
     vh = torch.empty(S.n, dtype=torch.float32, device=dev)
     rho = torch.empty(S.n, dtype=torch.float32, device=dev)
     eh = torch.empty((), dtype=torch.float64, device=dev)
@@ -507,7 +537,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32, b passes f16x2-split",
+            "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else
+                     ("f32, b passes f16 hi/lo split" if args.tc_parts == "fp16" else "f32, b passes bf16 3-part split"),
             "data": "synthetic",
             "config": {"workload": wl_text + (", FP32" if args.precision == "fp32" else
                                               ", FP32 with tensor-core split b passes") +
@@ -522,7 +554,8 @@ def main():
             "kernels_ms": kernels_ms, "batched": batched, "adjoint": adjoint, "other_grids": other,
             "solve_ms_ortho360": other["ortho360"]["solve_ms"] if other else None,
             "solve_ms_paper420": other["paper420"]["solve_ms"] if other else None,
-            "reorder_ms": reorder_ms,
+            "reorder_ms": reorder_ms, "reorder_device_ms": reorder_device_ms,
+            "reorder_device_equals_host": reorder_device_equal,
             "eh": float(eh.item()),
         }
         print(json.dumps(line), flush=True)

@@ -84,8 +84,9 @@ typedef struct {
 } hartree_desc;
 
 /* HARTREE_FP32_TC_SPLIT operands: FP16 hi/lo pairs with a power-of-two scale per
- * row by default (about 2^-22 relative per product); this flag selects BF16
- * hi/lo pairs instead (about 2^-16 relative per product, no scaling). */
+ * row by default (three products, about 2^-22 relative per product); this flag
+ * selects BF16 operands split in three parts instead (the six products of order
+ * <= 2, about 2^-24 relative per product, no scaling, twice the tensor work). */
 #define HARTREE_FLAG_TC_BF16 1u
 
 /* ---------------------------------------------------------------- plans */
@@ -124,6 +125,27 @@ unsigned long long hartree_plan_workspace_bytes(hartree_plan plan);
  * p W_k >= ceil(p/2) W; the axis sign makes its largest component positive.
  */
 int hartree_atoms_reorder(const double* pos, const double* w, int n, int n_leaves, int* perm, int* leaf_start);
+
+/*
+ * The same decomposition on the device (Sec. 3.1.2-3.1.5), for atoms that
+ * move between solves: one kernel launch per level of the bisection tree
+ * (ceil(log2 n_leaves) + 1 launches), one CTA per node, FP64 reductions for
+ * the centre of mass and the moment matrix, the host's 3x3 Jacobi solver for
+ * the principal axis, a bitonic sort by (t, atom index) and the same cut.
+ * Asynchronous on `stream`; allocates nothing (the plan's workspace holds the
+ * scratch); reads nothing back, so it can be captured in a CUDA graph.
+ *   plan       supplies the scratch; n and n_leaves must not exceed its max_atoms
+ *   pos        device [n][3] positions in Bohr (used as given; must be finite)
+ *   w          device [n] weights >= 0, or NULL for all 1
+ *   perm       device [n] out: atom indices in leaf order
+ *   leaf_start device [n_leaves + 1] out, as hartree_atoms_reorder
+ * The result equals hartree_atoms_reorder's wherever the projections t of two
+ * atoms of one node are not tied to within the last bits of the sums (the
+ * device sums the centre of mass and the moments in a different order).
+ * HARTREE_ERR_INVALID for null pointers or counts out of range.
+ */
+int hartree_atoms_reorder_device(hartree_plan plan, const double* pos, const double* w, int n, int n_leaves,
+                                 int* perm, int* leaf_start, void* stream);
 
 /* ---------------------------------------------------------------- single solves */
 

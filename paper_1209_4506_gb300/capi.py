@@ -34,6 +34,7 @@ EXPORTED = (
     "hartree_plan_destroy",
     "hartree_plan_workspace_bytes",
     "hartree_atoms_reorder",
+    "hartree_atoms_reorder_device",
     "hartree_splat",
     "hartree_solve_density",
     "hartree_solve",
@@ -98,6 +99,7 @@ def lib():
             L.hartree_plan_workspace_bytes.argtypes = [_vp]
             L.hartree_plan_workspace_bytes.restype = ctypes.c_ulonglong
             L.hartree_atoms_reorder.argtypes = [_vp, _vp, _i, _i, _vp, _vp]
+            L.hartree_atoms_reorder_device.argtypes = [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp]
             L.hartree_splat.argtypes = [_vp, _vp, _vp, _i, _vp, _vp]
             L.hartree_solve_density.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.hartree_solve.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]
@@ -144,6 +146,7 @@ hartree_plan_create = _call("hartree_plan_create")
 hartree_plan_destroy = _call("hartree_plan_destroy")
 hartree_plan_workspace_bytes = _call("hartree_plan_workspace_bytes")
 hartree_atoms_reorder = _call("hartree_atoms_reorder")
+hartree_atoms_reorder_device = _call("hartree_atoms_reorder_device")
 hartree_splat = _call("hartree_splat")
 hartree_solve_density = _call("hartree_solve_density")
 hartree_solve = _call("hartree_solve")

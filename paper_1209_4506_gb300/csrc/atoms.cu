@@ -362,7 +362,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : NT == 128 ? (KP <= 5 
     T* wf = reinterpret_cast<T*>(smem_raw);  // [3][ld] image-summed fac
     T* wd = wf + 3 * ld;                     // [3][ld] image-summed dfac
     __shared__ double red[4][NT / 32];
-    const int atom = blockIdx.x / slabs, slab = blockIdx.x - atom * slabs;
+    const int blk = blockIdx.x / slabs, slab = blockIdx.x - blk * slabs;
+    const int atom = a.order ? a.order[blk] : blk;
     const AtomPrep<T> p = a.prep[atom];
     const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
     int nw[3], st[3];
@@ -515,6 +516,54 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : NT == 128 ? (KP <= 5 
     }
 }
 
+// The force gather's CTA order: atoms by the wrapped a start of their box (a counting sort by a
+// index; the order inside one a index is that of the atomics).  The gather streams each box slice
+// by slice along a, so CTAs resident together then read the same a slices of V, which stay in L2
+// while every atom that overlaps them uses them.  Each CTA computes one atom's sums alone, so the
+// results do not depend on this order.  One CTA of kOrderThreads threads; N1 <= kMaxAxis bins.
+constexpr int kOrderThreads = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kOrderThreads) k_slab_order(const AtomPrep<T>* __restrict__ prep, int n, int n1,
+                                                              int* __restrict__ order) {
+    __shared__ int bin[kMaxAxis];
+    __shared__ int wsum[kOrderThreads / 32];
+    for (int b = threadIdx.x; b < n1; b += kOrderThreads) bin[b] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kOrderThreads) atomicAdd(&bin[prep[i].st[0]], 1);
+    __syncthreads();
+    // exclusive scan of the bins: each thread a contiguous chunk, warp scans of the chunk sums
+    const int chunk = (n1 + kOrderThreads - 1) / kOrderThreads;
+    const int b0 = threadIdx.x * chunk, b1 = min(n1, b0 + chunk);
+    int local = 0;
+    for (int b = b0; b < b1; ++b) local += bin[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < kOrderThreads / 32 ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        if (lane < kOrderThreads / 32) wsum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int run = incl - local + (warp > 0 ? wsum[warp - 1] : 0);  // exclusive start of this thread's chunk
+    for (int b = b0; b < b1; ++b) {
+        const int c = bin[b];
+        bin[b] = run;
+        run += c;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kOrderThreads) order[atomicAdd(&bin[prep[i].st[0]], 1)] = i;
+}
+
 __global__ void k_forces_finalize(const double* __restrict__ part, int n, int slabs, const double* __restrict__ q,
                                   double dV, double norm, double inv_s2, double* __restrict__ f,
                                   double* __restrict__ phi) {
@@ -648,7 +697,9 @@ cudaError_t forces_impl(const Plan& p, const double* pos, const double* q, int n
     if (slabs > p.max_force_slabs) slabs = p.max_force_slabs;
     if (slabs < 1) slabs = 1;
     if (slabs == 1) {  // one CTA per atom writes its forces: no partials, no finalize launch
-        p.launches += 1;
+        p.launches += 2;
+        k_slab_order<T><<<1, kOrderThreads, 0, s>>>(a.prep, n, p.n[0], p.force_order);
+        a.order = p.force_order;
         launch_k_forces<T>(p, a, static_cast<const T*>(vh), (unsigned)n, 1, f, phi, s);
         return cudaGetLastError();
     }

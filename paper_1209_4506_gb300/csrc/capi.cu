@@ -131,7 +131,7 @@ void free_plan(Plan& p) {
     void* ptrs[] = {p.W,           p.R,        p.tw[0],         p.tw[1], p.tw[2], p.twp[0], p.twp[1], p.twp[2], p.gsq[0],
                     p.gsq[1],      p.gsq[2],   p.eh_partials,   p.leaf_box,
                     p.atom_prep,   p.atom_fac, p.atom_dfac, p.force_partials, p.d_pos,   p.d_q,   p.d_f,   p.d_eh,
-                    p.d_err,       p.bin_cursor, p.bin_list, p.tc_dft};
+                    p.d_err,       p.bin_cursor, p.bin_list, p.tc_dft, p.bisect, p.force_order};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -292,6 +292,7 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         {&p.atom_fac, (size_t)p.max_atoms * 3 * p.box_max * p.real_size},
         {&p.atom_dfac, (size_t)p.max_atoms * 3 * p.box_max * p.real_size},
         {(void**)&p.force_partials, (size_t)(p.max_atoms + p.max_force_slabs) * 4 * sizeof(double)},
+        {(void**)&p.force_order, (size_t)p.max_atoms * sizeof(int)},
         {(void**)&p.d_pos, (size_t)p.max_atoms * 3 * sizeof(double)},
         {(void**)&p.d_q, (size_t)p.max_atoms * sizeof(double)},
         {(void**)&p.d_f, (size_t)p.max_atoms * 3 * sizeof(double)},
@@ -300,6 +301,7 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         {(void**)&p.bin_cursor, (size_t)p.n_tiles * sizeof(int)},
         {(void**)&p.bin_list, (size_t)p.n_tiles * kBinCap * sizeof(int4)},
         {&p.tc_dft, p.prec == HARTREE_FP32_TC_SPLIT ? tc_table_bytes() : 16},
+        {&p.bisect, bisect_scratch_bytes(p.max_atoms)},
     };
     for (auto& a : allocs) {
         cudaError_t e = cudaMalloc(a.ptr, a.bytes);
@@ -327,6 +329,7 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
         if (e == cudaSuccess) e = configure_atom_kernels(p);
         if (e == cudaSuccess) e = configure_tc_kernels(p);
         if (e == cudaSuccess) e = upload_tc_tables(p);
+        if (e == cudaSuccess) e = configure_bisect();
         if (e != cudaSuccess) st = cuda_fail(e, "plan_create: kernel attributes");
     }
     if (st != HARTREE_OK) {
@@ -423,6 +426,17 @@ int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, v
         return fail(HARTREE_ERR_INVALID, "solve_pass: grids must be aligned to %d bytes", (int)(2 * plan->p.real_size));
     cudaError_t e = launch_poisson_pass(plan->p, pass, rho, vh, (cudaStream_t)stream);
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "solve_pass");
+}
+
+int hartree_atoms_reorder_device(hartree_plan plan, const double* pos, const double* w, int n, int n_leaves,
+                                 int* perm, int* leaf_start, void* stream) {
+    if (!plan || !leaf_start || (n > 0 && (!pos || !perm)))
+        return fail(HARTREE_ERR_INVALID, "atoms_reorder_device: null argument");
+    if (n < 0 || n > plan->p.max_atoms || n_leaves < 1 || n_leaves > plan->p.max_atoms)
+        return fail(HARTREE_ERR_INVALID, "atoms_reorder_device: n = %d, n_leaves = %d outside [0 / 1, max_atoms = %d]",
+                    n, n_leaves, plan->p.max_atoms);
+    cudaError_t e = launch_bisect(plan->p, pos, w, n, n_leaves, perm, leaf_start, (cudaStream_t)stream);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "atoms_reorder_device");
 }
 
 unsigned long long hartree_plan_launch_count(hartree_plan plan) { return plan ? plan->p.launches : 0ULL; }

@@ -143,6 +143,7 @@ struct AtomArgs {
     T* dfac;            // [n][3][fb]: d_m exp(-d_m^2/s^2)
     int fb;             // row length of fac / dfac (largest box extent)
     int* leaf;          // [nleaves][6]: start a, b, c (unwrapped), length a, b, c (points)
+    const int* order = nullptr;  // force gather: CTA -> atom (atoms by the a start of their box), or identity
 };
 
 struct Plan {
@@ -167,6 +168,7 @@ struct Plan {
     void* atom_dfac = nullptr;  // T[max_atoms][3][box_max]
     int* leaf_box = nullptr;    // [max_leaves][6]
     double* force_partials = nullptr;
+    int* force_order = nullptr;  // [max_atoms]: the force gather's CTA order (k_slab_order)
     int max_force_slabs = 0;
     int box_max = 0;          // largest per-axis point count of one atom's cutoff box
     double* d_pos = nullptr;  // staging for the host step
@@ -191,7 +193,8 @@ struct Plan {
     int n_tiles = 0;
     int* bin_cursor = nullptr;  // [n_tiles] atoms that reached each tile (may exceed kBinCap)
     int4* bin_list = nullptr;   // [n_tiles][kBinCap]: atom index, then st | cnt << 16 along a, b, c
-    void* tc_dft = nullptr;     // HARTREE_FP32_TC_SPLIT: BF16 hi/lo 16-point DFT operands (forward, inverse)
+    void* tc_dft = nullptr;     // HARTREE_FP32_TC_SPLIT: 16-bit split 16-point DFT operands (forward, inverse)
+    void* bisect = nullptr;     // scratch of the device atom reorder (bisect_scratch_bytes(max_atoms))
 };
 
 // Let kernel `f` use all of the device's opt-in shared memory that its static
@@ -239,6 +242,11 @@ int pass_variant(const Plan& p, int pass);  // the variant pass 0..4 runs under 
 void prepare_tma(Plan& p);                   // encode the tensor maps of the TMA-streamed passes
 long long launch_fast_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
 cudaError_t configure_atom_kernels(const Plan& p);
+// device atom reorder (reorder_dev.cu): modified recursive bisection, one launch per tree level
+size_t bisect_scratch_bytes(int max_atoms);
+cudaError_t configure_bisect();
+cudaError_t launch_bisect(const Plan& p, const double* pos, const double* w, int n, int n_leaves, int* perm,
+                          int* leaf_start, cudaStream_t s);
 // paired-lane TMA column passes (pair_passes.cu), FP32: b (passes 1, 3) and a (pass 2)
 int col_pair_variants(int n);
 bool col_pair_available(const Plan& p, int axis);

@@ -209,12 +209,12 @@ __device__ __forceinline__ c2 ptwmul(c2 a, const float4* tw, int lo) {
     const float4 h = tw[0];
     const float2 hr{h.x, h.y}, hi{h.z, h.w};
     if constexpr (INV) {
-        const float2 nar = sub2(make_float2(0.f, 0.f), a.re);
+        const float2 nar = mul2(a.re, make_float2(-1.f, -1.f));
         return c2{fma2(a.re, hr, mul2(a.im, hi)), fma2(a.im, hr, mul2(nar, hi))};
     } else {
         const float4 l = tw[lo];
         const float2 lr{l.x, l.y}, li{l.z, l.w};
-        const float2 nai = sub2(make_float2(0.f, 0.f), a.im);
+        const float2 nai = mul2(a.im, make_float2(-1.f, -1.f));
         return c2{fma2(a.re, hr, fma2(nai, hi, fma2(a.re, lr, mul2(nai, li)))),
                   fma2(a.re, hi, fma2(a.im, hr, fma2(a.re, li, mul2(a.im, lr))))};
     }
@@ -585,12 +585,14 @@ __global__ void __launch_bounds__(NT* G, MINB)
             auto green = [&](int j, int r, int k1, c2& v) {
                 const float4 gq = GA[k1];
                 const float2 G2 = add2(add2(make_float2(gq.x, gq.y), gbc_h), add2(make_float2(gq.z, gq.w), gbc_l));
-                // 1 / G2: hardware estimate and one Newton step (e = 1 - G2 r0 exact through the fma)
+                // 1 / G2: hardware estimate r0 and one Newton step r0 + r0 (1 - G2 r0), written as
+                // r0 - r0 ne with ne = G2 r0 - 1 exact through the fma
                 float2 r0;
                 asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0.x) : "f"(G2.x));
                 asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0.y) : "f"(G2.y));
-                const float2 e = fma2(sub2(make_float2(0.f, 0.f), G2), r0, dup(1.f));
-                float2 inv = fma2(r0, e, r0);
+                const float2 m1 = make_float2(-1.f, -1.f);
+                const float2 ne = fma2(G2, r0, m1);
+                float2 inv = fma2(mul2(r0, m1), ne, r0);
                 if (r == 0 && zero_g && j == 0) inv.x = 0.f;  // the neutralising background: G = 0 dropped
                 tsum = fma2(fma2(v.im, v.im, mul2(v.re, v.re)), inv, tsum);
                 const float2 sc = mul2(inv, gs);
