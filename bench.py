@@ -504,9 +504,11 @@ def main():
     alg = {"splat": 4.0 * ntot, "pass0_c_r2c": 4.0 * ntot + half, "pass1_b_fwd": 2 * half,
            "pass2_a_green": 2 * half, "pass3_b_inv": 2 * half, "pass4_c_c2r": half + 4.0 * ntot,
            "forces": 4.0 * ntot}
-    kernel_names = {"splat": "k_leaf_setup + k_splat_binned", "pass0_c_r2c": "k_r2c_fast/k_r2c_stream", "pass1_b_fwd": "k_col_fast/k_col_tma MODE 0",
-                    "pass2_a_green": "k_col_fast/k_col_tma MODE 2", "pass3_b_inv": "k_col_fast/k_col_tma MODE 1",
-                    "pass4_c_c2r": "k_c2r_fast/k_c2r_stream", "forces": "k_forces<float>"}
+    kernel_names = {"splat": "k_leaf_setup + k_splat_binned", "pass0_c_r2c": "k_r2c_fast/k_r2c_stream",
+                    "pass1_b_fwd": "k_col_fast/k_col_tma/k_col_pair MODE 0",
+                    "pass2_a_green": "k_col_fast/k_col_tma/k_col_pair MODE 2",
+                    "pass3_b_inv": "k_col_fast/k_col_tma/k_col_pair MODE 1",
+                    "pass4_c_c2r": "k_c2r_fast/k_c2r_stream", "forces": "k_slab_order + k_forces<float>"}
     dom = max(names, key=lambda k: kernels_ms[k])
     pk, src = peaks()
     achieved = alg[dom] / (kernels_ms[dom] * 1e-3) / 1e9
