@@ -1,5 +1,6 @@
 // fast_passes.cu -- compile-time specialised Poisson passes for line lengths
-// 16 .. 1024 that are powers of two (the cubic 32^3, 256^3 and 512^3 grids).
+// 16 .. 1024 that are powers of two (the cubic 32^3, 256^3 and 512^3 grids) and for
+// the mixed lengths of the other workloads (360, 384, 400, 420, 840 and their halves).
 //
 // Same five-pass schedule as poisson.cu (Sec. 2.1 / Sec. 3.2.4: c, b, a with
 // the Green multiply and E_H, b^-1, c^-1), but every radix, stage stride and
@@ -885,6 +886,7 @@ bool with_line_stream_cfg(int m, int variant, F&& f) {
         case 512: f(LineStreamCfg<8, 256, 8, 8, 8, 2>{}); return true;
         case 200: f(LineStreamCfg<16, 256, 8, 5, 5, 2>{}); return true;
         case 105: f(LineStreamCfg<16, 256, 3, 5, 7, 2>{}); return true;
+        case 210: f(LineStreamCfg<16, 256, 6, 5, 7, 2>{}); return true;
         default: return false;
     }
 }
@@ -965,6 +967,10 @@ bool with_col_tma_cfg(int n, int variant, F&& f) {
             if (variant == 1) f(ColTmaCfg<256, 12, 5, 7, 2, 8, 3>{});
             else f(ColTmaCfg<256, 12, 5, 7, 3, 8, 2>{});
             return true;
+        case 840:  // 12 x 7 x 10 or 10 x 7 x 12: 70 / 84, 120 and 84 / 70 butterflies per column
+            if (variant == 1) f(ColTmaCfg<512, 10, 7, 12, 2, 8, 1>{});
+            else f(ColTmaCfg<512, 12, 7, 10, 2, 8, 1>{});
+            return true;
         default: return false;
     }
 }
@@ -992,13 +998,14 @@ bool with_col_cfg(int n, int variant, F&& f) {
         case 1024: f(ColCfg<T, 8, 512, 16, 8, 8>{}); return true;
         case 360: f(ColCfg<T, d ? 8 : 16, 256, 8, 5, 9>{}); return true;
         case 420: f(ColCfg<T, 8, 256, 12, 5, 7>{}); return true;
+        case 840: f(ColCfg<T, d ? 4 : 8, 512, 12, 7, 10>{}); return true;
         case 384: f(ColCfg<T, d ? 8 : 16, d ? 256 : 512, 16, 8, 3>{}); return true;
         default: return false;
     }
 }
 int col_variants(int n) { return (n == 256 || n == 512) ? 2 : 1; }
 int col_tma_variants(int n) {
-    return n == 512 ? 6 : (n == 256 ? 3 : (n == 360 ? 3 : (n == 384 || n == 420 ? 2 : 0)));
+    return n == 512 ? 6 : (n == 256 ? 3 : (n == 360 ? 3 : (n == 384 || n == 420 || n == 840 ? 2 : 0)));
 }
 
 // Variants col_variants(n) .. of the b / a passes: the TMA-streamed kernels (FP32, plan has the tensor maps).
@@ -1034,6 +1041,7 @@ bool with_line_cfg(int m, int variant, F&& f) {
         case 1024: f(LineCfg<T, 4, 256, 16, 8, 8>{}); return true;
         case 200: f(LineCfg<T, 16, 256, 8, 5, 5>{}); return true;
         case 105: f(LineCfg<T, 16, 256, 3, 5, 7>{}); return true;
+        case 210: f(LineCfg<T, 16, 256, 6, 5, 7>{}); return true;
         default: return false;
     }
 }

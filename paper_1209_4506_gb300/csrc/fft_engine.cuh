@@ -213,6 +213,57 @@ __host__ __device__ __forceinline__ void dft12(cpx<T>* v) {
     }
 }
 
+// Radix 6 as 2 x 3: with n = 3 n1 + n2 and k = k1 + 2 k2, three 2-point DFTs over n1, the
+// twiddles w6^(n2 k1) (w6 = exp(-+ 2 pi i / 6)), then two 3-point DFTs over n2.
+template <typename T, bool INV, bool COMP = true>
+__host__ __device__ __forceinline__ void dft6(cpx<T>* v) {
+    const double h = 0.866025403784438646764;  // sin(pi / 3)
+    const double sg = INV ? 1.0 : -1.0;
+    cpx<T> y[3][2];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2) {
+        y[n2][0] = v[n2] + v[n2 + 3];
+        y[n2][1] = v[n2] - v[n2 + 3];
+    }
+    y[1][1] = kcmul<T, COMP>(y[1][1], 0.5, sg * h);   // w6^1
+    y[2][1] = kcmul<T, COMP>(y[2][1], -0.5, sg * h);  // w6^2
+#pragma unroll
+    for (int k1 = 0; k1 < 2; ++k1) {
+        cpx<T> t[3] = {y[0][k1], y[1][k1], y[2][k1]};
+        dft3<T, INV, COMP>(t);
+        v[k1] = t[0];
+        v[k1 + 2] = t[1];
+        v[k1 + 4] = t[2];
+    }
+}
+
+// Radix 10 as 2 x 5: with n = 5 n1 + n2 and k = k1 + 2 k2, five 2-point DFTs over n1, the
+// twiddles w10^(n2 k1), then two 5-point DFTs over n2.
+template <typename T, bool INV, bool COMP = true>
+__host__ __device__ __forceinline__ void dft10(cpx<T>* v) {
+    // cos and sin of 2 pi m / 10, m = 1 .. 4
+    const double C[5] = {1.0, 0.80901699437494742410229341718282, 0.30901699437494742410229341718282,
+                         -0.30901699437494742410229341718282, -0.80901699437494742410229341718282};
+    const double S[5] = {0.0, 0.58778525229247312916870595463907, 0.95105651629515357211643933337938,
+                         0.95105651629515357211643933337938, 0.58778525229247312916870595463907};
+    const double sg = INV ? 1.0 : -1.0;
+    cpx<T> y[5][2];
+#pragma unroll
+    for (int n2 = 0; n2 < 5; ++n2) {
+        y[n2][0] = v[n2] + v[n2 + 5];
+        y[n2][1] = v[n2] - v[n2 + 5];
+    }
+#pragma unroll
+    for (int n2 = 1; n2 < 5; ++n2) y[n2][1] = kcmul<T, COMP>(y[n2][1], C[n2], sg * S[n2]);  // w10^n2
+#pragma unroll
+    for (int k1 = 0; k1 < 2; ++k1) {
+        cpx<T> t[5] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1], y[4][k1]};
+        dft5<T, INV, COMP>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 5; ++k2) v[k1 + 2 * k2] = t[k2];
+    }
+}
+
 // Radix 9 as 3 x 3: with n = 3 n1 + n2 and k = k1 + 3 k2, three 3-point DFTs over
 // n1, the twiddles w9^(n2 k1), then three 3-point DFTs over n2.
 template <typename T, bool INV, bool COMP = true>
@@ -321,9 +372,11 @@ __host__ __device__ __forceinline__ void dft(cpx<T>* v) {
     if constexpr (R == 3) dft3<T, INV, COMP>(v);
     if constexpr (R == 4) dft4<T, INV, COMP>(v);
     if constexpr (R == 5) dft5<T, INV, COMP>(v);
+    if constexpr (R == 6) dft6<T, INV, COMP>(v);
     if constexpr (R == 7) dft7<T, INV, COMP>(v);
     if constexpr (R == 8) dft8<T, INV, COMP>(v);
     if constexpr (R == 9) dft9<T, INV, COMP>(v);
+    if constexpr (R == 10) dft10<T, INV, COMP>(v);
     if constexpr (R == 12) dft12<T, INV, COMP>(v);
     if constexpr (R == 16) dft16<T, INV, COMP>(v);
     if constexpr (R == 32) dft32<T, INV, COMP>(v);
