@@ -1265,7 +1265,7 @@ bool encode_tensor_map_3d(CUtensorMap* map, void* base, const uint64_t dims[3], 
 }
 
 // Tensor maps over the half spectrum W (FP32, viewed as floats [N1][N2][2 ldc]) for the b and a
-// column passes: boxes of 16 or 8 complex columns by up to 256 rows.
+// column passes: boxes of 16, 8 or 4 complex columns by up to 256 rows.
 void prepare_tma(Plan& p) {
     p.tma_ok = false;
     if (p.prec == HARTREE_FP64) return;
@@ -1275,10 +1275,14 @@ void prepare_tma(Plan& p) {
     const uint32_t box_a[3] = {32, 1, (uint32_t)box_rows(p.n[0])};
     const uint32_t box_b8[3] = {16, (uint32_t)box_rows(p.n[1]), 1};
     const uint32_t box_a8[3] = {16, 1, (uint32_t)box_rows(p.n[0])};
+    const uint32_t box_b4[3] = {8, (uint32_t)box_rows(p.n[1]), 1};
+    const uint32_t box_a4[3] = {8, 1, (uint32_t)box_rows(p.n[0])};
     const bool ok_b = encode_tensor_map_3d(&p.tmap_b, p.W, dims, strides, box_b) &&
-                      encode_tensor_map_3d(&p.tmap_b8, p.W, dims, strides, box_b8);
+                      encode_tensor_map_3d(&p.tmap_b8, p.W, dims, strides, box_b8) &&
+                      encode_tensor_map_3d(&p.tmap_b4, p.W, dims, strides, box_b4);
     const bool ok_a = encode_tensor_map_3d(&p.tmap_a, p.W, dims, strides, box_a) &&
-                      encode_tensor_map_3d(&p.tmap_a8, p.W, dims, strides, box_a8);
+                      encode_tensor_map_3d(&p.tmap_a8, p.W, dims, strides, box_a8) &&
+                      encode_tensor_map_3d(&p.tmap_a4, p.W, dims, strides, box_a4);
     p.tma_ok = ok_a && ok_b && p.d_err != nullptr && p.sm_count > 0;
 }
 

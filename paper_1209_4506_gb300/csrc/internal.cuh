@@ -186,6 +186,7 @@ struct Plan {
     bool tma_ok = false;      // tensor maps over W are valid
     CUtensorMap tmap_b, tmap_a;    // 16-column boxes of the TMA-streamed b and a passes
     CUtensorMap tmap_b8, tmap_a8;  // 8-column boxes
+    CUtensorMap tmap_b4, tmap_a4;  // 4-column boxes
     // use_fast: bit 0: c passes, bit 1: b passes, bit 2: a pass use the specialised kernels
     size_t smem_c, smem_b, smem_a;
     // tile bins of the splat: per 16 x 8 x 32 tile up to kBinCap atoms whose cutoff box reaches it

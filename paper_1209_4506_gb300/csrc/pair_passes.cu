@@ -226,10 +226,11 @@ __device__ __forceinline__ c2 ptwmul(c2 a, const float4* tw, int lo) {
 // rows o + r NS (r < R).  The accessors turn a run into one or two base rows per thread, so
 // every access is a base register plus an immediate offset:
 //   lbase<NB>(j)        physical row of j, the run's first load (the others add r NB);
-//   sbase<NS, R>(o, j)  physical rows sb[0], sb[1] of the two parity classes of the store run,
+//   sbase<NS, R>(o, j)  physical rows sb[0 .. NC) of the NC classes of the store run,
 //                       cls<NS>(r) the class of row o + r NS (which then sits at sb[cls] + r NS).
 template <int COLS>
 struct NatPair {
+    static constexpr int NC = 1;
     float* t;
     int p;
     template <int NB>
@@ -252,17 +253,21 @@ struct NatPair {
         *reinterpret_cast<float4*>(t + (n * COLS + 2 * p) * 2) = make_float4(v.re.x, v.im.x, v.re.y, v.im.y);
     }
 };
-// Split layout: row n lives at physical row n ^ ((n >> SH) & 1) (SH = 0: no swizzle).
+// Split layout: row n lives at physical row n ^ ((n >> SH) & M) (SH = 0: no swizzle), M + 1 the
+// rows of a 128-byte line: 2 for 8-column tiles (64-byte rows), 4 for 4-column tiles.
 template <int COLS, int SH>
 struct SplitPair {
+    static constexpr int M = COLS == 4 ? 3 : 1;
+    static constexpr int NC = SH > 0 ? M + 1 : 1;
+    static_assert(SH == 0 || (1 << SH) > M, "the swizzle must stay below bit SH");
     float* t;
     int p;
     template <int NB>
     __device__ __forceinline__ int lbase(int j) const {
         if constexpr (SH > 0) {
-            // j < NB and NB a multiple of 2^(SH+1): adding r NB leaves the swizzle bit of j alone
-            static_assert(NB % (2 << SH) == 0, "load run stride");
-            return j ^ ((j >> SH) & 1);
+            // j < NB and NB a multiple of (M + 1) 2^SH: adding r NB leaves the swizzle bits of j alone
+            static_assert(NB % ((M + 1) << SH) == 0, "load run stride");
+            return j ^ ((j >> SH) & M);
         } else {
             return j;
         }
@@ -270,19 +275,21 @@ struct SplitPair {
     template <int NS, int R>
     __device__ __forceinline__ void sbase(int o, int j, int* sb) const {
         if constexpr (SH == 0) {
-            sb[0] = sb[1] = o;
+            sb[0] = o;
         } else if constexpr (NS == 1) {
-            // rows j R + r, R = 2^SH: the swizzle bit is j's lowest bit, flipping r's lowest bit
+            // rows j R + r, R = 2^SH: the swizzle j & M flips the low bits of r, so the rows of
+            // class c = r & M sit at o + (c ^ (j & M)) + (r - c)
             static_assert(R == (1 << SH), "store run of a first stage");
-            const int jb = j & 1;
-            sb[0] = o + jb;
-            sb[1] = o - jb;
+            const int x = j & M;
+#pragma unroll
+            for (int c = 0; c <= M; ++c) sb[c] = o + ((c ^ x) - c);
         } else {
-            // NS a multiple of 2^SH: the swizzle bit of o + r NS is that of o flipped by r NS / 2^SH
+            // NS a multiple of 2^SH: the swizzle of o + r NS is ((o >> SH) + r NS / 2^SH) & M, and
+            // it only touches bits below SH, which r NS leaves clear
             static_assert(NS % (1 << SH) == 0, "store run stride");
-            const int b = (o >> SH) & 1;
-            sb[0] = o ^ b;
-            sb[1] = o ^ b ^ 1;
+            const int b = (o >> SH) & M;
+#pragma unroll
+            for (int c = 0; c <= M; ++c) sb[c] = o ^ ((b + c) & M);
         }
     }
     template <int NS>
@@ -290,9 +297,9 @@ struct SplitPair {
         if constexpr (SH == 0)
             return 0;
         else if constexpr (NS == 1)
-            return r & 1;
+            return r & M;
         else
-            return (r * (NS >> SH)) & 1;
+            return (r * (NS >> SH)) & M;
     }
     __device__ __forceinline__ c2 ldp(int n) const {
         const float4 x = *reinterpret_cast<const float4*>(t + (n * COLS + 2 * p) * 2);
@@ -303,16 +310,21 @@ struct SplitPair {
     }
 };
 
+#pragma nv_diag_suppress 177  // the inverse-table offsets are unused by the b passes
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
+
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+// Tile buffers of a group of k_col_pair: the ring slots, a work buffer (PP = 1, 2), or three
+// rotating buffers (PP = 3).
+__host__ __device__ constexpr int pair_bufs(int nbuf, int pp) { return pp == 3 ? 3 : nbuf + (pp > 0 ? 1 : 0); }
 
 // Stage tables of a column transform of radices R0 R1 R2 (R2 = 1: two stages), in entries of
 // 32 bytes: stage 2 (R1, NS = R0) at f2, stage 3 (R2, NS = R0 R1) at f3; for MODE 2 the
 // inverse transform's stages (radices reversed) follow unless they equal the forward ones.
-#pragma nv_diag_suppress 177  // the inverse-table offsets are unused by the b passes
 template <int R0, int R1, int R2, int MODE>
 struct PairTwLayout {
     static constexpr int N = R0 * R1 * R2;
@@ -386,8 +398,10 @@ struct GroupSync {
 // tw: the stage's table (unused for NS = 1).
 // `hook` runs once every thread has read src (after the barrier); with a hook, each thread first
 // orders its reads of src before later async-proxy writes to it (a TMA refill of the buffer).
-template <int N, int R, int NS, int JSTEP, bool INV, bool COMP, class Src, class Dst, class Sync,
-          class Hook = NoHook>
+// INPLACE = false: src and dst are different buffers and nobody writes src before the caller's
+// next barrier, so the stage needs no barrier of its own (unless a hook must run after the reads).
+template <int N, int R, int NS, int JSTEP, bool INV, bool COMP, bool INPLACE = true, class Src, class Dst,
+          class Sync, class Hook = NoHook>
 __device__ __forceinline__ void pstage(const Src& src, const Dst& dst, int j0, const float4* tw, int lo,
                                        const Sync& bar, const Hook& hook = Hook{}) {
     constexpr int NB = N / R;
@@ -402,8 +416,9 @@ __device__ __forceinline__ void pstage(const Src& src, const Dst& dst, int j0, c
 #pragma unroll
         for (int r = 0; r < R; ++r) v[t][r] = src.ldp(lb + r * NB);
     }
-    if constexpr (!std::is_same<Hook, NoHook>::value) fence_proxy_async_smem();
-    bar.sync();
+    constexpr bool HOOK = !std::is_same<Hook, NoHook>::value;
+    if constexpr (HOOK) fence_proxy_async_smem();
+    if constexpr (INPLACE || HOOK) bar.sync();
     hook();
 #pragma unroll
     for (int t = 0; t < BPT; ++t) {
@@ -416,7 +431,7 @@ __device__ __forceinline__ void pstage(const Src& src, const Dst& dst, int j0, c
         }
         pdft<R, INV, COMP>(v[t]);
         const int o = (j - k) * R + k;
-        int sb[2];
+        int sb[Dst::NC];
         dst.template sbase<NS, R>(o, j, sb);
 #pragma unroll
         for (int r = 0; r < R; ++r) dst.stp(sb[Dst::template cls<NS>(r)] + r * NS, v[t][r]);
@@ -426,9 +441,9 @@ __device__ __forceinline__ void pstage(const Src& src, const Dst& dst, int j0, c
 // The last forward stage (radix R, NS = N / R: butterfly j's outputs sit at j + r NS), the
 // Green multiply on each output, and the inverse transform's first stage (radix R, no
 // twiddles), whose inputs are exactly the points this thread holds.
-template <int N, int R, int JSTEP, class Sp, class Green, class Sync>
-__device__ __forceinline__ void pstage_pivot(const Sp& sp, int j0, const float4* tw, int lo, const Green& green,
-                                             const Sync& bar) {
+template <int N, int R, int JSTEP, bool INPLACE = true, class Sp, class Dp, class Green, class Sync>
+__device__ __forceinline__ void pstage_pivot(const Sp& sp, const Dp& dp, int j0, const float4* tw, int lo,
+                                             const Green& green, const Sync& bar) {
     constexpr int NS = N / R;
     constexpr int BPT = (NS + JSTEP - 1) / JSTEP;
     constexpr bool GUARD = NS % JSTEP != 0;
@@ -441,7 +456,7 @@ __device__ __forceinline__ void pstage_pivot(const Sp& sp, int j0, const float4*
 #pragma unroll
         for (int r = 0; r < R; ++r) v[t][r] = sp.ldp(lb + r * NS);
     }
-    bar.sync();
+    if constexpr (INPLACE) bar.sync();
 #pragma unroll
     for (int t = 0; t < BPT; ++t) {
         const int j = j0 + t * JSTEP;
@@ -454,10 +469,10 @@ __device__ __forceinline__ void pstage_pivot(const Sp& sp, int j0, const float4*
 #pragma unroll
         for (int r = 0; r < R; ++r) green(j, r, j + r * NS, v[t][r]);
         pdft<R, true, false>(v[t]);
-        int sb[2];
-        sp.template sbase<1, R>(j * R, j, sb);
+        int sb[Dp::NC];
+        dp.template sbase<1, R>(j * R, j, sb);
 #pragma unroll
-        for (int r = 0; r < R; ++r) sp.stp(sb[Sp::template cls<1>(r)] + r, v[t][r]);
+        for (int r = 0; r < R; ++r) dp.stp(sb[Dp::template cls<1>(r)] + r, v[t][r]);
     }
 }
 
@@ -470,7 +485,16 @@ __device__ __forceinline__ void pstage_pivot(const Sp& sp, int j0, const float4*
 // (p, j0) of a group transforms column pair p.
 // MODE 0: forward along b, 1: inverse along b, 2: forward along a, Green multiply, E_H
 // partial, inverse along a.  Every mbarrier wait is bounded (error word, early exit).
-template <int COLS, int NT, int R0, int R1, int R2, int MODE, int NBUF, int MINB, int G>
+// PP > 0: each group also owns a work buffer, and the stages alternate between the ring slot and
+// it (slot -> work -> slot -> ...), so a stage's reads and writes never meet and it needs one
+// barrier instead of two.  The last stage writes the work buffer, which the TMA store drains.  The
+// slot is refilled with the group's next tile as soon as the last stage has read it (PP = 1, one
+// more barrier), or with the store (PP = 2).
+// PP = 3: three buffers per group take turns: tile k arrives in buffer k % 3 and is transformed
+// through buffer (k + 2) % 3, whose result the TMA store takes at the start of tile k + 1 (the
+// barrier that starts a tile also ends the previous one); buffer (k + 1) % 3 is refilled with
+// tile k + 1 once that store has read it, during tile k's second stage.  NBUF is unused.
+template <int COLS, int NT, int R0, int R1, int R2, int MODE, int NBUF, int MINB, int G, int PP>
 __global__ void __launch_bounds__(NT* G, MINB)
     k_col_pair(FastArgs<float> a, const __grid_constant__ CUtensorMap tmap, int ntiles, int chunks, int* err) {
     constexpr int N = R0 * R1 * R2;
@@ -480,18 +504,20 @@ __global__ void __launch_bounds__(NT* G, MINB)
     constexpr int NBOX = N / BOXR;
     constexpr int TILE = N * COLS * 2;  // floats per tile buffer
     constexpr uint32_t TILE_BYTES = (uint32_t)N * COLS * 8;
-    constexpr int SH = COLS == 8 ? ilog2(R0) : 0;  // row swizzle of the split layout (64-byte rows)
-    static_assert(COLS == 8 || COLS == 16, "tiles of 8 or 16 columns");
+    constexpr int SH = COLS <= 8 ? ilog2(R0) : 0;  // row swizzle of the split layout (32- or 64-byte rows)
+    static_assert(COLS == 4 || COLS == 8 || COLS == 16, "tiles of 4, 8 or 16 columns");
     static_assert(SH == 0 || (R2 > 1 ? R0 == R2 : R0 == R1), "the row swizzle assumes mirrored radices");
+    static_assert(PP == 0 || R2 > 1, "the ping-pong chain is written for three-stage transforms");
+    constexpr int NB = pair_bufs(NBUF, PP);  // tile buffers (and mbarriers) per group
     using L = PairTwLayout<R0, R1, R2, MODE>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    float* bufs = reinterpret_cast<float*>(base);  // [G][NBUF][TILE]
-    float4* TW = reinterpret_cast<float4*>(bufs + G * NBUF * TILE);
+    float* bufs = reinterpret_cast<float*>(base);  // [G][NB][TILE]: the ring slots, then the work buffer
+    float4* TW = reinterpret_cast<float4*>(bufs + G * NB * TILE);
     float4* GA = TW + 2 * L::total;  // MODE 2: |G_a|^2 per a index as (h, h, l, l)
     constexpr int lo = L::total;     // the twiddles' remainders follow their rounded values
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(GA + (MODE == 2 ? N : 0));  // [G][NBUF]
-    double* red = reinterpret_cast<double*>(mbar + G * NBUF);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(GA + (MODE == 2 ? N : 0));  // [G][NB]
+    double* red = reinterpret_cast<double*>(mbar + G * NB);
     fill_pair_tables<R0, R1, R2, MODE>(TW, MODE == 2 ? a.twpa : a.twpb, NT * G);
     if constexpr (MODE == 2)
         for (int k = threadIdx.x; k < N; k += NT * G) {
@@ -499,14 +525,14 @@ __global__ void __launch_bounds__(NT* G, MINB)
             GA[k] = make_float4(g.re, g.re, g.im, g.im);
         }
     if (threadIdx.x == 0) {
-        for (int b = 0; b < G * NBUF; ++b) mbar_init(&mbar[b], 1);
+        for (int b = 0; b < G * NB; ++b) mbar_init(&mbar[b], 1);
         fence_barrier_init();
     }
     __syncthreads();
     const int g = threadIdx.x / NT, lt = threadIdx.x - g * NT;
     const GroupSync<G, NT> bar{g};
-    float* gbufs = bufs + g * NBUF * TILE;
-    uint64_t* gbar = mbar + g * NBUF;
+    float* gbufs = bufs + g * NB * TILE;
+    uint64_t* gbar = mbar + g * NB;
     const int worker = blockIdx.x * G + g, nworkers = gridDim.x * G;
     auto issue_load = [&](int t, int b) {
         const int line = t / chunks, c0 = (t - line * chunks) * COLS;
@@ -519,9 +545,8 @@ __global__ void __launch_bounds__(NT* G, MINB)
                 tma_load_3d(dst + h * BOXR * COLS * 2, &tmap, &gbar[b], 2 * c0, h * BOXR, line);
         }
     };
-    auto issue_store = [&](int t, int b) {
+    auto issue_store = [&](int t, const float* src) {
         const int line = t / chunks, c0 = (t - line * chunks) * COLS;
-        const float* src = gbufs + b * TILE;
         for (int h = 0; h < NBOX; ++h) {
             if (MODE == 2)
                 tma_store_3d(&tmap, src + h * BOXR * COLS * 2, 2 * c0, line, h * BOXR);
@@ -531,35 +556,83 @@ __global__ void __launch_bounds__(NT* G, MINB)
         tma_commit();
     };
     if (lt == 0)
-        for (int b = 0; b < NBUF; ++b) {
+        for (int b = 0; b < (PP == 3 ? 1 : NBUF); ++b) {
             const int t = worker + b * nworkers;
             if (t < ntiles) issue_load(t, b);
         }
     const int p = lt % P, j0 = lt / P;
     uint32_t parity = 0;
     float2 sum = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);  // E_H, compensated across tiles
+    int pend = -1, pend_b = 0;  // PP = 3: the tile whose result waits in buffer pend_b for its store
     for (int k = 0;; ++k) {
         const int t = worker + k * nworkers;
         if (t >= ntiles) break;
-        const int b = k % NBUF;
-        const bool ok = mbar_wait(&gbar[b], (parity >> b) & 1u, err);
-        if (!bar.sync_and(ok)) {
+        const int b = PP == 3 ? k % 3 : k % NBUF;
+        const uint32_t phase = PP == 3 ? (uint32_t)(k / 3) & 1u : (parity >> b) & 1u;
+        const bool ok = mbar_wait(&gbar[b], phase, err);
+        if constexpr (PP == 1 || PP == 2)
+            if (lt == 0) tma_wait_read<0>();  // the work buffer is free once the last store has read it
+        const bool all_ok = bar.sync_and(ok);
+        if constexpr (PP == 3) {
+            // every thread of the group has finished the previous tile (and fenced its writes)
+            if (lt == 0 && pend >= 0) issue_store(pend, gbufs + pend_b * TILE);
+            pend = -1;
+        }
+        if (!all_ok) {
             // a load did not arrive: wait (bounded again) for this group's copies still in flight, then leave
-            if (lt == 0)
-                for (int i = 0; i < NBUF; ++i) {
-                    const int kk = k + i;
-                    if (worker + kk * nworkers < ntiles) mbar_wait(&gbar[kk % NBUF], (uint32_t)(kk / NBUF) & 1u, err);
+            if (lt == 0) {
+                if constexpr (PP == 3) {
+                    mbar_wait(&gbar[b], phase, err);
+                } else {
+                    for (int i = 0; i < NBUF; ++i) {
+                        const int kk = k + i;
+                        if (worker + kk * nworkers < ntiles)
+                            mbar_wait(&gbar[kk % NBUF], (uint32_t)(kk / NBUF) & 1u, err);
+                    }
                 }
+            }
             break;
         }
         parity ^= 1u << b;
         float* tile = gbufs + b * TILE;
+        float* work = gbufs + (PP == 3 ? (k + 2) % 3 : NBUF) * TILE;  // PP > 0 only
         const NatPair<COLS> nat{tile, p};
         const SplitPair<COLS, SH> spl{tile, p};
+        const NatPair<COLS> wnat{work, p};
+        const SplitPair<COLS, SH> wsp{work, p};
+        // PP = 1, 2: refill the slot with this group's tile k + NBUF once the last stage has read it
+        auto refill = [&] {
+            if (lt == 0) {
+                const int tn = worker + (k + NBUF) * nworkers;
+                if (tn < ntiles) issue_load(tn, b);
+            }
+        };
+        // PP = 3, after the first stage: once the previous tile's store has read buffer (k + 1) % 3,
+        // load tile k + 1 into it
+        auto early = [&] {
+            if constexpr (PP == 3)
+                if (lt == 0) {
+                    const int tn = t + nworkers;
+                    if (tn < ntiles) {
+                        tma_wait_read<0>();
+                        issue_load(tn, (k + 1) % 3);
+                    }
+                }
+        };
         if constexpr (MODE != 2) {
             constexpr bool INV = MODE == 1;
             constexpr bool COMP = !INV;
-            if constexpr (R2 == 1) {
+            if constexpr (PP > 0) {
+                pstage<N, R0, 1, JSTEP, INV, COMP, false>(nat, wsp, j0, TW, lo, bar);
+                bar.sync();
+                early();
+                pstage<N, R1, R0, JSTEP, INV, COMP, false>(wsp, spl, j0, TW + L::f2, lo, bar);
+                bar.sync();
+                if constexpr (PP == 1)
+                    pstage<N, R2, R0 * R1, JSTEP, INV, COMP, false>(spl, wnat, j0, TW + L::f3, lo, bar, refill);
+                else
+                    pstage<N, R2, R0 * R1, JSTEP, INV, COMP, false>(spl, wnat, j0, TW + L::f3, lo, bar);
+            } else if constexpr (R2 == 1) {
                 pstage<N, R0, 1, JSTEP, INV, COMP>(nat, spl, j0, TW, lo, bar);
                 bar.sync();
                 pstage<N, R1, R0, JSTEP, INV, COMP>(spl, nat, j0, TW + L::f2, lo, bar);
@@ -598,10 +671,24 @@ __global__ void __launch_bounds__(NT* G, MINB)
                 const float2 sc = mul2(inv, gs);
                 v = c2{mul2(v.re, sc), mul2(v.im, sc)};
             };
-            if constexpr (R2 == 1) {
+            if constexpr (PP > 0) {
+                pstage<N, R0, 1, JSTEP, false, true, false>(nat, wsp, j0, TW, lo, bar);
+                bar.sync();
+                early();
+                pstage<N, R1, R0, JSTEP, false, true, false>(wsp, spl, j0, TW + L::f2, lo, bar);
+                bar.sync();
+                pstage_pivot<N, R2, JSTEP, false>(spl, wsp, j0, TW + L::f3, lo, green, bar);
+                bar.sync();
+                pstage<N, R1, R2, JSTEP, true, false, false>(wsp, spl, j0, TW + L::i2, lo, bar);
+                bar.sync();
+                if constexpr (PP == 1)
+                    pstage<N, R0, R2 * R1, JSTEP, true, false, false>(spl, wnat, j0, TW + L::i3, lo, bar, refill);
+                else
+                    pstage<N, R0, R2 * R1, JSTEP, true, false, false>(spl, wnat, j0, TW + L::i3, lo, bar);
+            } else if constexpr (R2 == 1) {
                 pstage<N, R0, 1, JSTEP, false, true>(nat, spl, j0, TW, lo, bar);
                 bar.sync();
-                pstage_pivot<N, R1, JSTEP>(spl, j0, TW + L::f2, lo, green, bar);
+                pstage_pivot<N, R1, JSTEP>(spl, spl, j0, TW + L::f2, lo, green, bar);
                 bar.sync();
                 pstage<N, R0, R1, JSTEP, true, false>(spl, nat, j0, TW + L::i2, lo, bar);
             } else {
@@ -609,7 +696,7 @@ __global__ void __launch_bounds__(NT* G, MINB)
                 bar.sync();
                 pstage<N, R1, R0, JSTEP, false, true>(spl, spl, j0, TW + L::f2, lo, bar);
                 bar.sync();
-                pstage_pivot<N, R2, JSTEP>(spl, j0, TW + L::f3, lo, green, bar);
+                pstage_pivot<N, R2, JSTEP>(spl, spl, j0, TW + L::f3, lo, green, bar);
                 bar.sync();
                 pstage<N, R1, R2, JSTEP, true, false>(spl, spl, j0, TW + L::i2, lo, bar);
                 bar.sync();
@@ -625,15 +712,30 @@ __global__ void __launch_bounds__(NT* G, MINB)
             sum = s2;
         }
         fence_proxy_async_smem();
+        if constexpr (PP == 3) {
+            pend = t;
+            pend_b = (k + 2) % 3;
+            continue;  // the next tile's first barrier ends this one
+        }
         bar.sync();
         if (lt == 0) {
-            issue_store(t, b);
-            const int tn = worker + (k + NBUF) * nworkers;
-            if (tn < ntiles) {
-                tma_wait_read<0>();  // the buffer is free once the store has read it
-                issue_load(tn, b);
+            if constexpr (PP > 0) {
+                issue_store(t, work);
+            }
+            if constexpr (PP == 2) refill();
+            if constexpr (PP == 0) {
+                issue_store(t, tile);
+                const int tn = worker + (k + NBUF) * nworkers;
+                if (tn < ntiles) {
+                    tma_wait_read<0>();  // the buffer is free once the store has read it
+                    issue_load(tn, b);
+                }
             }
         }
+    }
+    if constexpr (PP == 3) {
+        bar.sync();
+        if (lt == 0 && pend >= 0) issue_store(pend, gbufs + pend_b * TILE);
     }
     if (lt == 0) tma_wait_all();
     if constexpr (MODE == 2) {
@@ -647,17 +749,18 @@ __global__ void __launch_bounds__(NT* G, MINB)
 }
 
 // ------------------------------------------------------------------ configurations
-template <int NT, int R0, int R1, int R2, int NBUF, int COLS, int MINB, int G = 1>
+template <int NT, int R0, int R1, int R2, int NBUF, int COLS, int MINB, int G = 1, int PP = 0>
 struct ColPairCfg {
     static constexpr int cols = COLS, n = R0 * R1 * R2, groups = G;
     static size_t smem(int mode) {
         const int tw = mode == 2 ? PairTwLayout<R0, R1, R2, 2>::total : PairTwLayout<R0, R1, R2, 0>::total;
-        return (size_t)G * NBUF * n * COLS * 8 + (size_t)tw * 32 + (mode == 2 ? (size_t)n * 16 : 0) + G * NBUF * 8 +
+        return (size_t)G * pair_bufs(NBUF, PP) * n * COLS * 8 + (size_t)tw * 32 +
+               (mode == 2 ? (size_t)n * 16 : 0) + G * pair_bufs(NBUF, PP) * 8 +
                (G * NT / 32) * sizeof(double) + 1024;
     }
     template <int MODE>
     static auto kernel() {
-        return k_col_pair<COLS, NT, R0, R1, R2, MODE, NBUF, MINB, G>;
+        return k_col_pair<COLS, NT, R0, R1, R2, MODE, NBUF, MINB, G, PP>;
     }
     static int resident(int mode) {
         static int r[3] = {0, 0, 0};
@@ -687,19 +790,24 @@ struct ColPairCfg {
 };
 
 // Paired variants by line length: one group per CTA (one or two ring slots, several CTAs per
-// SM), or one CTA per SM of several groups sharing the tables.
+// SM), or one CTA per SM of several groups sharing the tables, with or without work buffers.
 template <class F>
 bool with_col_pair_cfg(int n, int variant, F&& f) {
     switch (n) {
         case 256:  // 8 x 4 x 8: 32, 64 and 32 butterflies per column, none idle at 32 per pair
             if (variant == 1) f(ColPairCfg<128, 8, 4, 8, 2, 8, 1, 6>{});
-            else if (variant == 2) f(ColPairCfg<128, 8, 4, 8, 3, 8, 1, 4>{});
+            else if (variant == 2) f(ColPairCfg<128, 8, 4, 8, 1, 8, 1, 6, 1>{});
+            else if (variant == 3) f(ColPairCfg<128, 8, 4, 8, 2, 8, 1, 4, 2>{});
+            else if (variant == 4) f(ColPairCfg<64, 8, 4, 8, 2, 4, 1, 8, 2>{});
+            else if (variant == 5) f(ColPairCfg<64, 8, 4, 8, 2, 4, 1, 8, 3>{});
             else f(ColPairCfg<128, 8, 4, 8, 2, 8, 3>{});
             return true;
         case 512:
-            if (variant == 1) f(ColPairCfg<256, 8, 8, 8, 1, 8, 3>{});
-            else if (variant == 2) f(ColPairCfg<256, 8, 8, 8, 2, 8, 1, 3>{});
-            else if (variant == 3) f(ColPairCfg<256, 8, 8, 8, 3, 8, 1, 2>{});
+            if (variant == 1) f(ColPairCfg<256, 8, 8, 8, 2, 8, 1, 3>{});
+            else if (variant == 2) f(ColPairCfg<256, 8, 8, 8, 3, 8, 1, 2>{});
+            else if (variant == 3) f(ColPairCfg<256, 8, 8, 8, 1, 8, 1, 3, 1>{});
+            else if (variant == 4) f(ColPairCfg<256, 8, 8, 8, 2, 8, 1, 2, 2>{});
+            else if (variant == 5) f(ColPairCfg<256, 8, 8, 8, 2, 8, 1, 2, 3>{});
             else f(ColPairCfg<256, 8, 8, 8, 2, 8, 2>{});
             return true;
         default: return false;
@@ -708,7 +816,7 @@ bool with_col_pair_cfg(int n, int variant, F&& f) {
 
 }  // namespace
 
-int col_pair_variants(int n) { return n == 512 ? 4 : (n == 256 ? 3 : 0); }
+int col_pair_variants(int n) { return n == 512 || n == 256 ? 6 : 0; }
 
 bool col_pair_available(const Plan& p, int axis) {
     return p.prec != HARTREE_FP64 && p.tma_ok && col_pair_variants(p.n[axis]) > 0;
@@ -737,7 +845,9 @@ long long launch_col_pair(const Plan& p, int pass, int variant, const FastArgs<f
         const int slots = c.resident(mode) * p.sm_count;
         const int need = (ntiles + c.groups - 1) / c.groups;  // CTAs that all have work
         grid = need < slots ? need : slots;
-        const CUtensorMap& map = c.cols == 16 ? (axis == 0 ? p.tmap_a : p.tmap_b) : (axis == 0 ? p.tmap_a8 : p.tmap_b8);
+        const CUtensorMap& map = c.cols == 16  ? (axis == 0 ? p.tmap_a : p.tmap_b)
+                                 : c.cols == 8 ? (axis == 0 ? p.tmap_a8 : p.tmap_b8)
+                                               : (axis == 0 ? p.tmap_a4 : p.tmap_b4);
         c.launch(mode, (unsigned)grid, a, map, ntiles, chunks, p.d_err, s);
     });
     return grid;
