@@ -498,18 +498,36 @@ def main():
                 acc[k] += ev[i].elapsed_time(ev[i + 1])
     kernels_ms = {k: acc[k] / reps for k in names}
     solve_ms = sum(kernels_ms[k] for k in names[1:6])
+    # the step's own kernels (a plan with HARTREE_FLAG_FUSED_SPLAT runs the splat inside pass 0)
+    fused = plan.fused_splat
+    if fused:
+        kernels_ms["splat_r2c_fused"] = time_events(lambda: plan.splat_pass(pos, q), reps, stream)
+    step_names = (["splat_r2c_fused"] if fused else ["splat", "pass0_c_r2c"]) + names[2:]
+    # the opt-in fused splat on a plan of its own, against the two kernels it replaces
+    fused_splat = None
+    if not args.skip_side and args.precision == "fp32" and not fused:
+        fplan = HartreePlan(S.n, S.cell, S.sigma, "fp32", atoms_per_leaf=apl, max_atoms=S.n_atoms,
+                            flags=capi.HARTREE_FLAG_FUSED_SPLAT)
+        if fplan.fused_splat:
+            t_f = time_events(lambda: fplan.splat_pass(pos, q), reps, stream)
+            fused_splat = {"fused_ms": t_f, "separate_ms": kernels_ms["splat"] + kernels_ms["pass0_c_r2c"],
+                           "form": "HARTREE_FLAG_FUSED_SPLAT: atom setup + k_r2c_splat (density never in HBM) vs "
+                                   "atom setup + k_splat_binned + the r2c pass"}
+        fplan.close()
     # algorithmic bytes per launch (fp32): c passes read / write N real + N1 N2 (N3/2+1) complex, b / a read+write the
     # half spectrum; splat writes N; forces read V once
     half = 8.0 * S.n[0] * S.n[1] * (S.n[2] // 2 + 1)
     alg = {"splat": 4.0 * ntot, "pass0_c_r2c": 4.0 * ntot + half, "pass1_b_fwd": 2 * half,
            "pass2_a_green": 2 * half, "pass3_b_inv": 2 * half, "pass4_c_c2r": half + 4.0 * ntot,
-           "forces": 4.0 * ntot}
+           "forces": 4.0 * ntot, "splat_r2c_fused": half}
     kernel_names = {"splat": "k_leaf_setup + k_splat_binned", "pass0_c_r2c": "k_r2c_fast/k_r2c_stream",
                     "pass1_b_fwd": "k_col_fast/k_col_tma/k_col_pair MODE 0",
                     "pass2_a_green": "k_col_fast/k_col_tma/k_col_pair MODE 2",
                     "pass3_b_inv": "k_col_fast/k_col_tma/k_col_pair MODE 1",
-                    "pass4_c_c2r": "k_c2r_fast/k_c2r_stream", "forces": "k_slab_order + k_forces<float>"}
-    dom = max(names, key=lambda k: kernels_ms[k])
+                    "pass4_c_c2r": "k_c2r_fast/k_c2r_stream", "forces": "k_slab_order + k_forces<float>",
+                    "splat_r2c_fused": "k_leaf_setup + k_r2c_splat"}
+    # the roofline object: the longest kernel of the step as timed
+    dom = max(step_names, key=lambda k: kernels_ms[k])
     pk, src = peaks()
     achieved = alg[dom] / (kernels_ms[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": pk["hbm_gbs"],
@@ -553,7 +571,10 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "solve_ms": solve_ms, "solve_gbs": ybytes / (solve_ms * 1e-3) / 1e9,
             "solve_points_per_s": ntot / (solve_ms * 1e-3), "solve_roofline": solve_roofline,
-            "kernels_ms": kernels_ms, "batched": batched, "adjoint": adjoint, "other_grids": other,
+            "kernels_ms": kernels_ms, "step_kernels": step_names, "fused_splat": fused_splat,
+            "step_path": "splat fused into the r2c pass (no density grid)" if fused
+                         else "separate splat kernel and density grid",
+            "batched": batched, "adjoint": adjoint, "other_grids": other,
             "solve_ms_ortho360": other["ortho360"]["solve_ms"] if other else None,
             "solve_ms_paper420": other["paper420"]["solve_ms"] if other else None,
             "reorder_ms": reorder_ms, "reorder_device_ms": reorder_device_ms,

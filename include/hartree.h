@@ -80,7 +80,7 @@ typedef struct {
     int precision;        /* a hartree_precision                                            */
     int atoms_per_leaf;   /* atoms per bisection leaf used by the splat; 0 = default 16     */
     int max_atoms;        /* largest atom count any call on this plan will pass; 0 = 65536 */
-    unsigned flags;       /* 0, or HARTREE_FLAG_TC_BF16 with HARTREE_FP32_TC_SPLIT           */
+    unsigned flags;       /* 0 or a combination of the HARTREE_FLAG_* values below           */
 } hartree_desc;
 
 /* HARTREE_FP32_TC_SPLIT operands: FP16 hi/lo pairs with a power-of-two scale per
@@ -88,6 +88,16 @@ typedef struct {
  * selects BF16 operands split in three parts instead (the six products of order
  * <= 2, about 2^-24 relative per product, no scaling, twice the tensor work). */
 #define HARTREE_FLAG_TC_BF16 1u
+
+/* FP32 plans: calls that need no density grid (hartree_solve and hartree_step with
+ * rho = NULL, hartree_step_host, hartree_forces with vh = NULL) compute the density of
+ * each tile of c lines inside the first (r2c) pass, so rho never reaches device memory
+ * (the calculation flow of Sec. 3.2.4 without the A -> B grid).  Same results to FP32
+ * rounding.  Off by default: the separate splat and r2c kernels are faster on GB300
+ * (both are bound by instruction issue, not by the density's round trip through HBM).
+ * Ignored by FP64 plans and for c lengths N3 / 2 without a fused kernel (it exists for
+ * 60, 64, 105, 128, 200, 210 and 256). */
+#define HARTREE_FLAG_FUSED_SPLAT 2u
 
 /* ---------------------------------------------------------------- plans */
 
@@ -221,6 +231,21 @@ int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int
  * the other passes ignore both.  Returns HARTREE_ERR_INVALID for other pass ids.
  */
 int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, void* stream);
+
+/*
+ * The splat fused into pass 0 alone, for per-kernel timing and profiling: the
+ * atoms' boxes and factor arrays, then the kernel that computes the density of
+ * each tile of c lines and transforms it into the plan's half spectrum (what
+ * hartree_splat + pass 0 leave there, to FP32 rounding).  pos, q: device
+ * [n][3], [n] (bisection order).  Returns HARTREE_ERR_INVALID for null
+ * pointers or n outside [0, max_atoms], HARTREE_ERR_UNSUPPORTED_SIZE when the
+ * plan does not use the fused kernel (no HARTREE_FLAG_FUSED_SPLAT, FP64, or a
+ * c length N3 / 2 without one).
+ */
+int hartree_splat_pass(hartree_plan plan, const double* pos, const double* q, int n, void* stream);
+
+/* 1 if calls with no density grid use the splat fused into pass 0, else 0. */
+int hartree_plan_fused_splat(hartree_plan plan);
 
 /* Number of CUDA kernels this plan has launched so far (host-side count). */
 unsigned long long hartree_plan_launch_count(hartree_plan plan);

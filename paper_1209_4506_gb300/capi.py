@@ -27,6 +27,7 @@ HARTREE_ERR_TIMEOUT = 5
 HARTREE_ERR_NOT_CAPTURABLE = 6
 
 HARTREE_FLAG_TC_BF16 = 1
+HARTREE_FLAG_FUSED_SPLAT = 2
 
 # Every symbol the public header declares (the CPU tests check the exports).
 EXPORTED = (
@@ -42,6 +43,8 @@ EXPORTED = (
     "hartree_step",
     "hartree_step_host",
     "hartree_solve_pass",
+    "hartree_splat_pass",
+    "hartree_plan_fused_splat",
     "hartree_plan_launch_count",
     "hartree_solve_density_noalloc",
     "hartree_plan_autotune",
@@ -107,6 +110,8 @@ def lib():
             L.hartree_step.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
             L.hartree_step_host.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _vp]
             L.hartree_solve_pass.argtypes = [_vp, _i, _vp, _vp, _vp]
+            L.hartree_splat_pass.argtypes = [_vp, _vp, _vp, _i, _vp]
+            L.hartree_plan_fused_splat.argtypes = [_vp]
             L.hartree_plan_launch_count.argtypes = [_vp]
             L.hartree_plan_launch_count.restype = ctypes.c_ulonglong
             L.hartree_solve_density_noalloc.argtypes = [ctypes.POINTER(hartree_desc), _vp, _vp, _vp, _vp]
@@ -154,6 +159,8 @@ hartree_forces = _call("hartree_forces")
 hartree_step = _call("hartree_step")
 hartree_step_host = _call("hartree_step_host")
 hartree_solve_pass = _call("hartree_solve_pass")
+hartree_splat_pass = _call("hartree_splat_pass")
+hartree_plan_fused_splat = _call("hartree_plan_fused_splat")
 hartree_plan_launch_count = _call("hartree_plan_launch_count")
 hartree_solve_density_noalloc = _call("hartree_solve_density_noalloc")
 hartree_plan_autotune = _call("hartree_plan_autotune")

@@ -66,7 +66,8 @@ __device__ __forceinline__ AxisTiles axis_tiles(int lo, int cnt, int n, int T, i
 // One CTA per leaf (apl consecutive atoms in bisection order): the atoms' boxes
 // and factor arrays; the leaf's box (structure C of Sec. 3.2.2: the box around
 // the cutoff boxes of the leaf's atoms, each shifted to the periodic image
-// nearest the leaf's first atom); and, with `bins`, each atom appended to the
+// nearest the leaf's first atom; the fused splat selects atoms through these);
+// and, with `bins`, each atom appended to the
 // list of every splat tile its box reaches.  A list entry carries the atom's
 // wrapped box start and length per axis, so the splat reads the factors with no
 // further lookup.  Slots are taken with atomics, so a list is unordered (the
@@ -90,7 +91,6 @@ __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int
     const int runs = (a.fb + kRun<T>() - 1) / kRun<T>();
     const int ntask = (i1 - i0) * 3 * runs;
     for (int t = threadIdx.x; t < ntask; t += blockDim.x) atom_factors_one(a, (long long)i0 * 3 * runs + t);
-    if (!bins) return;
     const int ns[3] = {a.n1, a.n2, a.n3};
     for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x)
         for (int d = 0; d < 3; ++d) {
@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int
         a.leaf[6 * l + d] = bmin[d];
         a.leaf[6 * l + 3 + d] = min(bmax[d] - bmin[d], ns[d]);
     }
+    if (!bins) return;
     // one warp per atom appends it to its tiles' lists
     const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int i = i0 + (int)(threadIdx.x >> 5); i < i1; i += nwarps) {
@@ -747,6 +748,25 @@ cudaError_t configure_atom_kernels(const Plan& p) {
 
 cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s) {
     return p.prec == HARTREE_FP64 ? splat_impl<double>(p, pos, q, n, rho, s) : splat_impl<float>(p, pos, q, n, rho, s);
+}
+
+cudaError_t launch_splat_solve(const Plan& p, const double* pos, const double* q, int n, void* vh, double* eh,
+                               cudaStream_t s) {
+    if (!splat_fused_available(p)) {
+        cudaError_t e = launch_splat(p, pos, q, n, vh, s);
+        return e == cudaSuccess ? launch_poisson(p, vh, vh, eh, s) : e;
+    }
+    const cudaError_t e = launch_splat_r2c(p, pos, q, n, s);
+    return e == cudaSuccess ? launch_poisson_from(p, 1, nullptr, vh, eh, s) : e;
+}
+
+cudaError_t launch_splat_r2c(const Plan& p, const double* pos, const double* q, int n, cudaStream_t s) {
+    const AtomArgs<float> a = make_atom_args<float>(p, pos, q, n);
+    cudaError_t e = prep_atoms<float>(p, a, false, s);
+    if (e != cudaSuccess) return e;
+    p.launches += 1;
+    launch_r2c_splat(p, a, s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,

@@ -214,7 +214,8 @@ int hartree_plan_create(const hartree_desc* desc, hartree_plan* out) {
     if (!desc || !out) return fail(HARTREE_ERR_INVALID, "plan_create: null argument");
     *out = nullptr;
     const hartree_desc& d = *desc;
-    if (d.flags & ~HARTREE_FLAG_TC_BF16) return fail(HARTREE_ERR_INVALID, "plan_create: unknown flags");
+    if (d.flags & ~(HARTREE_FLAG_TC_BF16 | HARTREE_FLAG_FUSED_SPLAT))
+        return fail(HARTREE_ERR_INVALID, "plan_create: unknown flags");
     if ((d.flags & HARTREE_FLAG_TC_BF16) && d.precision != HARTREE_FP32_TC_SPLIT)
         return fail(HARTREE_ERR_INVALID, "plan_create: HARTREE_FLAG_TC_BF16 needs HARTREE_FP32_TC_SPLIT");
     if (d.precision != HARTREE_FP64 && d.precision != HARTREE_FP32 && d.precision != HARTREE_FP32_TC_SPLIT)
@@ -379,9 +380,13 @@ int hartree_solve(hartree_plan plan, const double* pos, const double* q, int n, 
         return fail(HARTREE_ERR_INVALID, "solve: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
     if (!grid_aligned(plan->p, rho) || !grid_aligned(plan->p, vh))
         return fail(HARTREE_ERR_INVALID, "solve: grids must be aligned to %d bytes", (int)(2 * plan->p.real_size));
-    void* dens = rho ? rho : vh;
-    cudaError_t e = launch_splat(plan->p, pos, q, n, dens, (cudaStream_t)stream);
-    if (e == cudaSuccess) e = launch_poisson(plan->p, dens, vh, eh, (cudaStream_t)stream);
+    cudaError_t e;
+    if (rho) {
+        e = launch_splat(plan->p, pos, q, n, rho, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = launch_poisson(plan->p, rho, vh, eh, (cudaStream_t)stream);
+    } else {
+        e = launch_splat_solve(plan->p, pos, q, n, vh, eh, (cudaStream_t)stream);
+    }
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "solve");
 }
 
@@ -394,8 +399,7 @@ int hartree_forces(hartree_plan plan, const double* pos, const double* q, int n,
     cudaError_t e = cudaSuccess;
     const bool recompute = vh == nullptr;
     if (recompute) {
-        e = launch_splat(plan->p, pos, q, n, plan->p.R, s);
-        if (e == cudaSuccess) e = launch_poisson(plan->p, plan->p.R, plan->p.R, nullptr, s);
+        e = launch_splat_solve(plan->p, pos, q, n, plan->p.R, nullptr, s);
         vh = plan->p.R;
     }
     // the splat of a recompute already prepared the atoms' boxes and factors
@@ -411,9 +415,13 @@ int hartree_step(hartree_plan plan, const double* pos, const double* q, int n, v
     if (!grid_aligned(plan->p, rho) || !grid_aligned(plan->p, vh))
         return fail(HARTREE_ERR_INVALID, "step: grids must be aligned to %d bytes", (int)(2 * plan->p.real_size));
     cudaStream_t s = (cudaStream_t)stream;
-    void* dens = rho ? rho : vh;
-    cudaError_t e = launch_splat(plan->p, pos, q, n, dens, s);
-    if (e == cudaSuccess) e = launch_poisson(plan->p, dens, vh, eh, s);
+    cudaError_t e;
+    if (rho) {
+        e = launch_splat(plan->p, pos, q, n, rho, s);
+        if (e == cudaSuccess) e = launch_poisson(plan->p, rho, vh, eh, s);
+    } else {
+        e = launch_splat_solve(plan->p, pos, q, n, vh, eh, s);
+    }
     if (e == cudaSuccess && n > 0) e = launch_forces(plan->p, pos, q, n, vh, f, phi, s, true);
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "step");
 }
@@ -427,6 +435,18 @@ int hartree_solve_pass(hartree_plan plan, int pass, const void* rho, void* vh, v
     cudaError_t e = launch_poisson_pass(plan->p, pass, rho, vh, (cudaStream_t)stream);
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "solve_pass");
 }
+
+int hartree_splat_pass(hartree_plan plan, const double* pos, const double* q, int n, void* stream) {
+    if (!plan || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "splat_pass: null argument");
+    if (n < 0 || n > plan->p.max_atoms)
+        return fail(HARTREE_ERR_INVALID, "splat_pass: n = %d outside [0, max_atoms = %d]", n, plan->p.max_atoms);
+    if (!splat_fused_available(plan->p))
+        return fail(HARTREE_ERR_UNSUPPORTED_SIZE, "splat_pass: the plan has no splat fused into pass 0");
+    cudaError_t e = launch_splat_r2c(plan->p, pos, q, n, (cudaStream_t)stream);
+    return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "splat_pass");
+}
+
+int hartree_plan_fused_splat(hartree_plan plan) { return plan && splat_fused_available(plan->p) ? 1 : 0; }
 
 int hartree_atoms_reorder_device(hartree_plan plan, const double* pos, const double* w, int n, int n_leaves,
                                  int* perm, int* leaf_start, void* stream) {
@@ -557,8 +577,7 @@ int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int
         e = cudaMemcpyAsync(p.d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(p.d_q, q, sizeof(double) * n, cudaMemcpyHostToDevice, s);
     }
-    if (e == cudaSuccess) e = launch_splat(p, p.d_pos, p.d_q, n, p.R, s);
-    if (e == cudaSuccess) e = launch_poisson(p, p.R, p.R, p.d_eh, s);
+    if (e == cudaSuccess) e = launch_splat_solve(p, p.d_pos, p.d_q, n, p.R, p.d_eh, s);
     if (e == cudaSuccess && f && n > 0) e = launch_forces(p, p.d_pos, p.d_q, n, p.R, p.d_f, nullptr, s, true);
     if (e == cudaSuccess) e = cudaMemcpyAsync(eh, p.d_eh, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && f && n > 0)

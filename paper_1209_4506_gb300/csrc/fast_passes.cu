@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "atoms_dev.cuh"
 #include "internal.cuh"
 #include "tma.cuh"
 
@@ -782,6 +783,273 @@ __global__ void __launch_bounds__(NT, MINB)
     }
 }
 
+
+// ------------------------------------------------------------------ splat fused into the r2c pass (FP32)
+// The density never reaches HBM: persistent CTAs walk units of up to SEG tiles, a tile being LINES
+// consecutive c lines at one a index (b = b0 .. b0 + nl - 1), and compute each tile's density in
+// shared memory before the r2c transform of those lines.
+//   * Per unit (one a index, SEG tiles along b) the CTA selects, in increasing atom index (the order
+//     of the binned splat), the atoms whose cutoff box covers the a index and meets the unit's b
+//     range: first the leaf boxes (structure C of Sec. 3.2.2) that do, then each of their atoms.
+//     A selected atom becomes a record in shared memory: its index, wrapped b and c box, a factor
+//     and q (pi s^2)^-3/2 split in two FP32 parts.
+//   * Per tile the records whose b box meets the tile are taken (in order) in batches of kb; a batch
+//     stages each atom's a x b factor per line and its image-summed c factors times q, and thread
+//     (g, u) adds, for its points 2u and 2u + 1 of the LG lines of group g, one paired FMA per atom
+//     and line.  A unit with more atoms than the records hold selects per tile instead, in rounds.
+//   * The sums go into the transform's padded work buffer; the lines take the same transform and
+//     post-processing as k_r2c_stream.
+constexpr int kFuseLines = 16;
+constexpr int kFuseSeg = 8;  // tiles per unit
+
+__host__ __device__ constexpr int next_pow2(int n) { return n <= 1 ? 1 : 2 * next_pow2((n + 1) / 2); }
+
+template <int LINES, int NT, int R0, int R1, int R2, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_r2c_splat(AtomArgs<float> at, FastArgs<float> a, int tiles_b, int nunits, int kb, int fsh, int cap, int img) {
+    constexpr int M = R0 * R1 * R2;
+    constexpr int TPL = NT / LINES;
+    constexpr int LDP = M + M / 16 + 1;
+    constexpr int PT = next_pow2(M);  // threads per line group of the splat
+    constexpr int GL = NT / PT;       // line groups
+    constexpr int LG = LINES / GL;    // lines per thread
+    static_assert(PT >= 32 && PT <= NT && LINES % GL == 0, "splat thread layout");
+    const int fcw = 1 << fsh;  // c factors staged per atom
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cpx<float>* S = reinterpret_cast<cpx<float>*>(smem_raw);
+    TwPair<float>* TW = reinterpret_cast<TwPair<float>*>(S + LINES * LDP);
+    float2* WL = reinterpret_cast<float2*>(TW + LineTwLayout<R0, R1, R2>::fwd);  // [kb][LINES]: (w, w)
+    int4* RI = reinterpret_cast<int4*>(WL + kb * LINES);  // [cap]: atom, b box, c box, a factor
+    float2* RQ = reinterpret_cast<float2*>(RI + cap);     // [cap]: q (pi s^2)^-3/2 as two FP32 parts
+    float* FC = reinterpret_cast<float*>(RQ + cap);       // [kb][fcw]
+    int2* AC = reinterpret_cast<int2*>(FC + kb * fcw);    // [kb]: wrapped c start, points
+    int* lst = reinterpret_cast<int*>(AC + kb);           // [NT]: selected leaves
+    int* cand = lst + NT;                                 // [NT]: selected records of a tile
+    __shared__ int wcnt[NT / 32];
+    __shared__ int nsel;
+    fill_line_tw_fwd<float, R0, R1, R2>(TW, a.twpc);
+    const TwPair<float>* TWP = TW + LineTwLayout<R0, R1, R2>::s2 + LineTwLayout<R0, R1, R2>::s3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // ordered compaction of the threads whose flag is set into out[base + ..]; returns the count
+    auto compact = [&](bool flag, int value, int* out, int base, int limit) -> int {
+        const unsigned bal = __ballot_sync(0xffffffffu, flag);
+        __syncthreads();  // earlier readers of wcnt / nsel / out are done
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int s = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                const int c = wcnt[w];
+                wcnt[w] = s;
+                s += c;
+            }
+            nsel = s;
+        }
+        __syncthreads();
+        const int pos = base + wcnt[warp] + __popc(bal & ((1u << lane) - 1u));
+        if (flag && pos < limit) out[pos] = value;
+        __syncthreads();
+        return nsel;
+    };
+    const int g = threadIdx.x / PT, u = threadIdx.x - g * PT;
+    const int c0 = 2 * u;           // this thread's points c0, c0 + 1 (u < M)
+    const int wc0 = 2 * (u & ~31);  // the first point of this warp's range of 64
+    const int l = threadIdx.x / TPL, j0 = threadIdx.x % TPL;
+    LineSmem<float> sm{S + l * LDP};
+    const long long fstride = at.fb;
+    const int upr = (tiles_b + kFuseSeg - 1) / kFuseSeg;  // units per a index
+    // does [s, s + len) mod n meet [t0, t0 + tn) (s, t0 in [0, n), len <= n)?  range_hits without a division
+    auto meets = [](int s, int len, int t0, int tn, int n) {
+        int d = t0 - s;
+        if (d < 0) d += n;
+        return d < len || d + tn > n;
+    };
+    // a record for atom i (the caller has checked its boxes)
+    auto make_record = [&](int i, int ia, int r) {
+        const AtomPrep<float>& p = at.prep[i];
+        const float fa = image_sum(at.fac + i * 3 * fstride, ia, p.st[0], p.cnt[0], a.n1);
+        RI[r] = make_int4(i, p.st[1] | (p.cnt[1] << 16), p.st[2] | (p.cnt[2] << 16), __float_as_int(fa));
+        RQ[r] = make_float2(p.qn, p.ql);
+    };
+    // the factor of box point g - st (wrapped) of a box starting at st with cnt points: one load when
+    // the boxes along this axis fit in the grid (wide: several images, summed)
+    auto factor = [](const float* f, int g, int st, int cnt, int n, bool wide) {
+        int m = g - st;
+        if (m < 0) m += n;
+        float v = m < cnt ? __ldg(f + m) : 0.f;
+        if (wide)
+            for (m += n; m < cnt; m += n) v += __ldg(f + m);
+        return v;
+    };
+    const bool wide_b = img & 2, wide_c = img & 4;
+    // stage records cand[bb .. bb + nb) and add them to this thread's points
+    auto add_batch = [&](int bb, int nb, int b0, int nl, float2* acc) {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < nb * LINES; e += NT) {
+            const int tt = e / LINES, ll = e - tt * LINES;
+            const int4 R = RI[cand[bb + tt]];
+            int bg = b0 + ll;
+            if (bg >= a.n2) bg -= a.n2;
+            const float fb = factor(at.fac + (R.x * 3 + 1) * fstride, bg, R.y & 0xffff, R.y >> 16, a.n2, wide_b);
+            const float w = ll < nl ? __int_as_float(R.w) * fb : 0.f;
+            WL[e] = make_float2(w, w);
+        }
+#pragma unroll 4
+        for (int e = threadIdx.x; e < (nb << fsh); e += NT) {
+            const int tt = e >> fsh, m = e & (fcw - 1);
+            const int r = cand[bb + tt];
+            const int4 R = RI[r];
+            const int st = R.z & 0xffff, cnt = R.z >> 16, nw = min(cnt, a.n3);
+            int cc = st + m;
+            if (cc >= a.n3) cc -= a.n3;
+            const float sc = m < nw ? factor(at.fac + (R.x * 3 + 2) * fstride, cc, st, cnt, a.n3, wide_c) : 0.f;
+            const float2 qq = RQ[r];
+            FC[e] = qq.x * sc + qq.y * sc;
+            if (m == 0) AC[tt] = make_int2(st, nw);
+        }
+        __syncthreads();
+        if (u < M) {
+            for (int tt = 0; tt < nb; ++tt) {
+                const int2 ac = AC[tt];
+                if (!meets(ac.x, ac.y, wc0, 64, a.n3)) continue;  // the same for the whole warp
+                int d0 = c0 - ac.x;
+                if (d0 < 0) d0 += a.n3;
+                const int d1 = d0 + 1 == a.n3 ? 0 : d0 + 1;
+                const float* fc = FC + tt * fcw;
+                const float2 fp = make_float2(d0 < ac.y ? fc[d0] : 0.f, d1 < ac.y ? fc[d1] : 0.f);
+                const float2* wl = WL + tt * LINES + g * LG;
+#pragma unroll
+                for (int i = 0; i < LG; ++i) acc[i] = __ffma2_rn(wl[i], fp, acc[i]);
+            }
+        }
+        __syncthreads();
+    };
+    // the atoms whose box covers index ia and meets [b0, b0 + nb_) along b, in increasing index, by
+    // rounds of at most NT: each round's atoms become records 0 .. cnt - 1 and go to `round`
+    auto select_rounds = [&](int ia, int b0, int nb_, auto&& round) {
+        for (int lb = 0; lb < at.nleaves; lb += NT) {
+            const int lf = lb + (int)threadIdx.x;
+            bool hit = false;
+            if (lf < at.nleaves) {
+                const int* bx = at.leaf + 6 * lf;
+                hit = range_hits(bx[0], bx[3], ia, 1, a.n1) && range_hits(bx[1], bx[4], b0, nb_, a.n2);
+            }
+            const int nlf = compact(hit, lf, lst, 0, NT);
+            const int ncand = nlf * at.apl;
+            for (int cb = 0; cb < ncand; cb += NT) {
+                const int c = cb + (int)threadIdx.x;
+                int atom = -1;
+                if (c < ncand) {
+                    const int i = lst[c / at.apl] * at.apl + c % at.apl;
+                    if (i < at.n) {
+                        const AtomPrep<float>& p = at.prep[i];
+                        if (range_hits(p.lo[0], p.cnt[0], ia, 1, a.n1) && range_hits(p.lo[1], p.cnt[1], b0, nb_, a.n2))
+                            atom = i;
+                    }
+                }
+                round(atom);
+            }
+        }
+    };
+    for (int k = 0;; ++k) {
+        const int un = blockIdx.x + k * gridDim.x;
+        if (un >= nunits) break;
+        const int ia = un / upr, tb0 = (un - ia * upr) * kFuseSeg, tb1 = min(tiles_b, tb0 + kFuseSeg);
+        const int bu0 = tb0 * LINES, bun = min(tb1 * LINES, a.n2) - bu0;
+        // the unit's records (or overflow: more atoms than cap)
+        int nrec = 0;
+        select_rounds(ia, bu0, bun, [&](int atom) {
+            const int cnt = compact(atom >= 0, atom, cand, 0, NT);
+            for (int e = threadIdx.x; e < cnt; e += NT)
+                if (nrec + e < cap) make_record(cand[e], ia, nrec + e);
+            nrec += cnt;
+        });
+        __syncthreads();  // the records are written
+        const bool overflow = nrec > cap;
+        for (int tb = tb0; tb < tb1; ++tb) {
+            const int b0 = tb * LINES, nl = min(LINES, a.n2 - b0);
+            float2 acc[LG];
+#pragma unroll
+            for (int i = 0; i < LG; ++i) acc[i] = make_float2(0.f, 0.f);
+            if (!overflow) {
+                for (int rb = 0; rb < nrec; rb += NT) {
+                    const int r = rb + (int)threadIdx.x;
+                    bool hit = false;
+                    if (r < nrec) {
+                        const int rb_ = RI[r].y;
+                        hit = meets(rb_ & 0xffff, min(rb_ >> 16, a.n2), b0, nl, a.n2);
+                    }
+                    const int nc = compact(hit, r, cand, 0, NT);
+                    for (int bb = 0; bb < nc; bb += kb) add_batch(bb, min(kb, nc - bb), b0, nl, acc);
+                }
+            } else {
+                select_rounds(ia, b0, nl, [&](int atom) {
+                    const int cnt = compact(atom >= 0, atom, cand, 0, NT);
+                    for (int e = threadIdx.x; e < cnt; e += NT) {
+                        make_record(cand[e], ia, e);
+                        cand[e] = e;
+                    }
+                    __syncthreads();
+                    for (int bb = 0; bb < cnt; bb += kb) add_batch(bb, min(kb, cnt - bb), b0, nl, acc);
+                });
+            }
+            // the tile's density as z[m] = rho[2m] + i rho[2m + 1], line by line in the work buffer
+            if (u < M) {
+#pragma unroll
+                for (int i = 0; i < LG; ++i) S[(g * LG + i) * LDP + pidx(u)] = mk(acc[i].x, acc[i].y);
+            }
+            __syncthreads();
+            const long long gline = (long long)ia * a.n2 + b0 + l;
+            const bool act = l < nl;
+            // M-point transform in place (twiddles exp(-2 pi i e / M) = entry 2e of the 2M-point table)
+            line_ftransform<float, R0, R1, R2, TPL, false, true>(sm, sm, sm, j0, static_cast<const TwPair<float>*>(TW));
+            __syncthreads();
+            // X[k] and X[M - k] from one pair of loads, as in k_r2c_fast
+            if (act) {
+                cpx<float>* out = a.W + gline * a.ldc;
+                for (int kk = j0; kk <= M / 2; kk += TPL) {
+                    const cpx<float> z1 = sm.ld_(0, kk);
+                    const cpx<float> z2 = conjg(sm.ld_(0, kk == 0 ? 0 : M - kk));
+                    const cpx<float> E = scale(z1 + z2, 0.5f);
+                    const cpx<float> d = z1 - z2;
+                    const cpx<float> O = mk(d.im * 0.5f, -d.re * 0.5f);
+                    const cpx<float> tq = twmul(O, TWP[kk], false);
+                    out[kk] = E + tq;
+                    out[M - kk] = conjg(E - tq);
+                }
+            }
+            __syncthreads();  // the work buffer is read before the next tile writes it
+        }
+        __syncthreads();  // the records are read before the next unit writes them
+    }
+}
+
+template <int NT, int R0, int R1, int R2, int MINB>
+struct SplatLineCfg {
+    static constexpr int m = R0 * R1 * R2, lines = kFuseLines;
+    static size_t smem(int kb, int fcw, int cap) {
+        return (size_t)lines * (m + m / 16 + 1) * sizeof(cpx<float>) +
+               (size_t)LineTwLayout<R0, R1, R2>::fwd * sizeof(TwPair<float>) + (size_t)kb * lines * sizeof(float2) +
+               (size_t)cap * (sizeof(int4) + sizeof(float2)) + (size_t)kb * fcw * sizeof(float) +
+               (size_t)kb * sizeof(int2) + 2 * NT * sizeof(int);
+    }
+    static auto kernel() { return k_r2c_splat<kFuseLines, NT, R0, R1, R2, MINB>; }
+};
+
+template <class F>
+bool with_splat_line_cfg(int M, F&& f) {
+    switch (M) {
+        case 256: f(SplatLineCfg<256, 16, 16, 1, 2>{}); return true;
+        case 128: f(SplatLineCfg<256, 16, 8, 1, 2>{}); return true;
+        case 210: f(SplatLineCfg<256, 6, 5, 7, 2>{}); return true;
+        case 200: f(SplatLineCfg<256, 8, 5, 5, 2>{}); return true;
+        case 105: f(SplatLineCfg<256, 3, 5, 7, 2>{}); return true;
+        case 64: f(SplatLineCfg<256, 8, 8, 1, 2>{}); return true;
+        case 60: f(SplatLineCfg<256, 4, 3, 5, 2>{}); return true;
+        default: return false;
+    }
+}
+
 // ------------------------------------------------------------------ dispatch
 template <typename T, int COLS, int NT, int R0, int R1, int R2>
 struct ColCfg {
@@ -1133,7 +1401,60 @@ cudaError_t configure_fast_kernels(const Plan& p) {
     int optin = 0;
     cudaError_t e = optin_smem(&optin);
     if (e != cudaSuccess) return e;
-    return p.prec == HARTREE_FP64 ? configure_fast_t<double>(p, optin) : configure_fast_t<float>(p, optin);
+    e = p.prec == HARTREE_FP64 ? configure_fast_t<double>(p, optin) : configure_fast_t<float>(p, optin);
+    if (e == cudaSuccess && splat_fused_available(p)) e = configure_splat_fused(p, optin);
+    return e;
+}
+
+// ------------------------------------------------------------------ the splat fused into the r2c pass
+bool splat_fused_available(const Plan& p) {
+    if (p.prec == HARTREE_FP64 || !(p.desc.flags & HARTREE_FLAG_FUSED_SPLAT) || p.sm_count <= 0) return false;
+    return with_splat_line_cfg(p.M, [](auto) {});
+}
+
+// Staging of the fused splat: 2^fsh c factors per atom (the box, at most N3 wrapped points, rounded
+// up to a power of two), kb atoms per batch (at most 16 KB of c factors) and cap atom records per
+// unit (24 KB).
+static void splat_fused_shape(const Plan& p, int* kb, int* fsh, int* cap) {
+    const int w = std::min(p.box_max, p.n[2]);
+    int sh = 1;
+    while ((1 << sh) < w) ++sh;
+    *fsh = sh;
+    *kb = std::max(1, std::min(32, 4096 >> sh));
+    *cap = 1024;
+}
+
+cudaError_t configure_splat_fused(const Plan& p, int optin) {
+    int kb = 0, fsh = 0, cap = 0;
+    splat_fused_shape(p, &kb, &fsh, &cap);
+    cudaError_t e = cudaSuccess;
+    with_splat_line_cfg(p.M, [&](auto c) {
+        if (c.smem(kb, 1 << fsh, cap) + 2048 > (size_t)optin) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) e = allow_max_dynamic_smem(c.kernel(), optin);
+    });
+    return e;
+}
+
+long long launch_r2c_splat(const Plan& p, const AtomArgs<float>& at, cudaStream_t s) {
+    int kb = 0, fsh = 0, cap = 0;
+    splat_fused_shape(p, &kb, &fsh, &cap);
+    const FastArgs<float> a = make_fast_args<float>(p, 0);
+    long long grid = -1;
+    with_splat_line_cfg(p.M, [&](auto c) {
+        const int tiles_b = (p.n[1] + c.lines - 1) / c.lines;
+        const int nunits = p.n[0] * ((tiles_b + kFuseSeg - 1) / kFuseSeg);
+        // axes along which a box can exceed the grid (several images of an atom on one point)
+        const int img = (p.box_max > p.n[0] ? 1 : 0) | (p.box_max > p.n[1] ? 2 : 0) | (p.box_max > p.n[2] ? 4 : 0);
+        const size_t sm = c.smem(kb, 1 << fsh, cap);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.kernel(), 256, sm) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        grid = std::min<long long>(nunits, (long long)per_sm * p.sm_count);
+        c.kernel()<<<(unsigned)grid, 256, sm, s>>>(at, a, tiles_b, nunits, kb, fsh, cap, img);
+    });
+    return grid;
 }
 
 // pass: 0 = c r2c (rho -> W), 1 = b forward, 2 = a with Green, 3 = b inverse, 4 = c c2r (W -> vh).

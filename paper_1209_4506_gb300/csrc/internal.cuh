@@ -218,10 +218,23 @@ inline cudaError_t optin_smem(int* bytes) {
 
 // launchers (poisson.cu / atoms.cu); return cudaSuccess or the launch error
 cudaError_t launch_poisson(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s);
+// The passes first .. 4 (the half spectrum W already holds pass first - 1's result) and E_H.
+cudaError_t launch_poisson_from(const Plan& p, int first, const void* rho, void* vh, double* eh, cudaStream_t s);
 cudaError_t launch_poisson_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s);
 // launch_splat prepares the per-atom boxes and factor arrays in the plan's workspace.
 // `prepared` (forces): they already hold these very positions (an earlier launch on the same stream).
 cudaError_t launch_splat(const Plan& p, const double* pos, const double* q, int n, void* rho, cudaStream_t s);
+// Splat, the five passes and E_H into vh, with no density grid: through the splat fused into the
+// r2c pass when the plan has it, else the splat into vh and the solve in place.
+cudaError_t launch_splat_solve(const Plan& p, const double* pos, const double* q, int n, void* vh, double* eh,
+                               cudaStream_t s);
+// The atoms' boxes, factors and leaf boxes, then the fused splat + r2c kernel (splat_fused_available).
+cudaError_t launch_splat_r2c(const Plan& p, const double* pos, const double* q, int n, cudaStream_t s);
+// The fused splat + r2c kernel (FP32 plans with HARTREE_FLAG_FUSED_SPLAT and a compiled kernel
+// for M): the atoms' boxes, factors and leaf boxes must be prepared.
+bool splat_fused_available(const Plan& p);
+cudaError_t configure_splat_fused(const Plan& p, int optin);
+long long launch_r2c_splat(const Plan& p, const AtomArgs<float>& at, cudaStream_t s);
 cudaError_t launch_forces(const Plan& p, const double* pos, const double* q, int n, const void* vh, double* f,
                           double* phi, cudaStream_t s, bool prepared = false);
 void set_last_error(const char* msg);  // the message hartree_last_error() returns on this thread

@@ -79,9 +79,9 @@ long long pass_impl(const Plan& p, int pass, const void* rho, void* vh, cudaStre
 }
 
 template <typename T>
-cudaError_t poisson_impl(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s) {
+cudaError_t poisson_impl(const Plan& p, int first, const void* rho, void* vh, double* eh, cudaStream_t s) {
     long long n_part = 0;
-    for (int pass = 0; pass < 5; ++pass) {
+    for (int pass = first; pass < 5; ++pass) {
         const long long g = pass_impl<T>(p, pass, rho, vh, s);
         if (pass == 2) n_part = g;
     }
@@ -107,7 +107,12 @@ cudaError_t configure_poisson(int optin) {
 }  // namespace
 
 cudaError_t launch_poisson(const Plan& p, const void* rho, void* vh, double* eh, cudaStream_t s) {
-    return p.prec == HARTREE_FP64 ? poisson_impl<double>(p, rho, vh, eh, s) : poisson_impl<float>(p, rho, vh, eh, s);
+    return launch_poisson_from(p, 0, rho, vh, eh, s);
+}
+
+cudaError_t launch_poisson_from(const Plan& p, int first, const void* rho, void* vh, double* eh, cudaStream_t s) {
+    return p.prec == HARTREE_FP64 ? poisson_impl<double>(p, first, rho, vh, eh, s)
+                                  : poisson_impl<float>(p, first, rho, vh, eh, s);
 }
 
 cudaError_t launch_poisson_pass(const Plan& p, int pass, const void* rho, void* vh, cudaStream_t s) {

@@ -186,6 +186,16 @@ class HartreePlan:
                                      _stream_handle(self.device)))
         return (vh, eh, f, phi) if want_phi else (vh, eh, f)
 
+    def splat_pass(self, pos, q):
+        """Launch the splat fused into pass 0 alone (atoms -> half spectrum); for timing and profiling."""
+        pos, q, n = self._atoms(pos, q)
+        capi.check(capi.hartree_splat_pass(self.handle, pos.data_ptr(), q.data_ptr(), n, _stream_handle(self.device)))
+
+    @property
+    def fused_splat(self) -> bool:
+        """True if steps with no density grid compute the density inside pass 0."""
+        return bool(capi.hartree_plan_fused_splat(self.handle))
+
     def solve_pass(self, pass_id: int, rho=None, vh=None):
         """Launch one Poisson pass alone (0: c r2c .. 4: c c2r); for timing and profiling."""
         if rho is not None:

@@ -6,7 +6,9 @@ atoms) and the 16x16x8 supercell on the paper's 420 x 420 x 210 grid (16,384
 atoms, sigma 0.8 Bohr, radix 7): atoms in the order of the modified recursive bisection with 16 atoms
 per leaf, kernel variants picked by the autotuner, and the whole step
 (splat, Poisson solve, E_H, forces) in one hartree_step call, against the
-FP64 oracle on the host cores with the same per-axis cutoff of 5 sigma.
+FP64 oracle on the host cores with the same per-axis cutoff of 5 sigma; then the same step
+on a plan with HARTREE_FLAG_FUSED_SPLAT (the splat fused into the r2c pass, no density grid)
+against the same oracle results.
 
 Bars (FP32 path): V_H and rho relative L2 <= 2e-6, E_H relative <= 1e-7,
 forces and dE_H/dq <= 1e-5 absolute.  Also checked: charge neutrality of the
@@ -71,6 +73,17 @@ def test_full_size_step_matches_oracle(name):
     # independent from atom to atom: a random walk bounded by eps_32 (6e-8) times sum |F| (the reading
     # of this bar is written out with the oracle's readings)
     assert np.max(np.abs(f_g.sum(axis=0))) <= 1e-7 * np.abs(f_o).sum()
+    plan.close()
+    # the same step with the splat fused into the r2c pass (no density grid), same bars
+    plan = HartreePlan(S.n, S.cell, S.sigma, "fp32", atoms_per_leaf=apl, max_atoms=S.n_atoms, flags=2)
+    assert plan.fused_splat
+    vh2, eh2, f2, phi2 = plan.step(pos, q, want_phi=True)
+    torch.cuda.synchronize()
+    plan.device_status()
+    assert rel_l2(vh2.double().cpu().numpy(), vh_o) <= 2e-6
+    assert abs(eh2.item() - eh_o) <= 1e-7 * abs(eh_o)
+    assert np.max(np.abs(f2.cpu().numpy()[inv] - f_o)) <= 1e-5
+    assert np.max(np.abs(phi2.cpu().numpy()[inv] - phi_o)) <= 1e-5
     plan.close()
 
 
