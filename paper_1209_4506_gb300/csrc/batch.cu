@@ -48,52 +48,66 @@ struct BatchArgs {
     uint32_t spin_limit;  // dependency-wait probes before a wait gives up
 };
 
-__global__ void __launch_bounds__(kThreads) k_batched(BatchArgs b, const double* pos, const double* q, float* vh,
-                                                      double* eh) {
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_batched(BatchArgs b, const double* pos, const double* q,
+                                                            float* vh, double* eh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kThreads / 32];
-    __shared__ long long s_item;
-    __shared__ int s_ok;
+    __shared__ int s_stage, s_cell, s_tile, s_ok;
+    // Thread 0 takes items, decodes them and waits for their dependencies; the CTA meets once per
+    // item before the work and once after it.  It takes the next item while the CTA works on the
+    // current one (always a later item in the queue, so the earliest unfinished item never waits
+    // on a held one), and it remembers the last (stage, cell) whose previous stage it saw complete:
+    // a CTA's consecutive items mostly share it, and then need no look at the counter.
+    long long next = 0;
+    int seen_s = -1, seen_c = -1;
+    if (threadIdx.x == 0) next = (long long)atomicAdd(b.head, 1ULL);
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(b.head, 1ULL);
-        __syncthreads();
-        const long long item = s_item;
-        if (item >= b.total) break;
-        // decode (stage, cell, tile)
-        const int stride = b.n_cells + 1;
-        int s = 0;
-        while (s + 1 < NST && item >= b.off[(s + 1) * stride]) ++s;
-        const long long* o = b.off + s * stride;
-        int lo = 0, hi = b.n_cells;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (o[mid] <= item)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const int c = lo;
-        const int t = (int)(item - o[c]);
-        const BatchCell& cell = b.cells[c];
         if (threadIdx.x == 0) {
-            int ok = 1;
-            if (s > 0) {
-                const int need = cell.cnt[s - 1];
-                volatile int* d = b.done + (s - 1) * b.n_cells + c;
-                uint32_t it = 0;
-                while (*d < need) {
-                    if (++it > b.spin_limit) {
-                        atomicOr(b.err, kErrTimeout);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(64);
+            const long long item = next;
+            int s = -1, c = 0, t = 0, ok = 1;
+            if (item < b.total) {
+                next = (long long)atomicAdd(b.head, 1ULL);
+                // decode (stage, cell, tile)
+                const int stride = b.n_cells + 1;
+                s = 0;
+                while (s + 1 < NST && item >= b.off[(s + 1) * stride]) ++s;
+                const long long* o = b.off + s * stride;
+                int lo = 0, hi = b.n_cells;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (o[mid] <= item)
+                        lo = mid;
+                    else
+                        hi = mid;
                 }
-                __threadfence();
+                c = lo;
+                t = (int)(item - o[c]);
+                if (s > 0 && !(s == seen_s && c == seen_c)) {
+                    const int need = b.cells[c].cnt[s - 1];
+                    volatile int* d = b.done + (s - 1) * b.n_cells + c;
+                    uint32_t it = 0;
+                    while (*d < need) {
+                        if (++it > b.spin_limit) {
+                            atomicOr(b.err, kErrTimeout);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                    __threadfence();
+                    if (ok) seen_s = s, seen_c = c;
+                }
             }
+            s_stage = s;
+            s_cell = c;
+            s_tile = t;
             s_ok = ok;
         }
         __syncthreads();
+        const int s = s_stage, c = s_cell, t = s_tile;
+        if (s < 0) break;
+        const BatchCell& cell = b.cells[c];
         if (s_ok) {
             const PoissonArgs<float>& pa = cell.pa;
             AtomArgs<float> aa = cell.aa;
@@ -134,7 +148,9 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchArgs b, const double*
 
 // ---------------------------------------------------------------- host side
 cudaError_t configure_batched(size_t smem) {
-    return cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_batched<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batched<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
 }
 
 struct BatchHost {
@@ -150,6 +166,7 @@ struct BatchHost {
     size_t smem = 0;
     int grid = 0;
     int n_cells = 0;
+    int minb = 2;                        // the kernel's register budget: 2 or 3 CTAs per SM
     int skip_stage = -1, skip_cell = 0;  // fault injection (hartree_batch_fault_inject)
     uint32_t spin_limit = kSpinLimit;
 };
@@ -257,7 +274,12 @@ extern "C" int hartree_batch_create(const hartree_desc* descs, const int* atom_c
     if (e == cudaSuccess) e = cudaMemset(h.err_d, 0, sizeof(int));
     if (e == cudaSuccess) e = configure_batched(h.smem);
     int per_sm = 0, dev = 0, sms = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, kThreads, h.smem);
+    // three CTAs per SM when the tiles' shared memory allows it (the registers are then capped at 80)
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<3>, kThreads, h.smem);
+    if (e == cudaSuccess && per_sm < 3)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<2>, kThreads, h.smem);
+    else
+        h.minb = 3;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
@@ -311,7 +333,10 @@ extern "C" int hartree_solve_batched(hartree_batch batch, const double* pos, con
         a.skip_stage = h.skip_stage;
         a.skip_cell = h.skip_cell;
         a.spin_limit = h.spin_limit;
-        k_batched<<<h.grid, kThreads, h.smem, s>>>(a, pos, q, static_cast<float*>(vh), eh);
+        if (h.minb == 3)
+            k_batched<3><<<h.grid, kThreads, h.smem, s>>>(a, pos, q, static_cast<float*>(vh), eh);
+        else
+            k_batched<2><<<h.grid, kThreads, h.smem, s>>>(a, pos, q, static_cast<float*>(vh), eh);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return batch_fail(HARTREE_ERR_CUDA, cudaGetErrorString(e));
