@@ -41,28 +41,6 @@ namespace hartree {
 
 namespace {
 
-// ---------------------------------------------------------------- tile binning
-// The tiles along one axis that hold at least one wrapped index of the box
-// [lo, lo + cnt): count of them, and tile(k) for k < count.
-struct AxisTiles {
-    int start, c1, count;
-    __device__ __forceinline__ int tile(int k) const { return k < c1 ? start + k : k - c1; }
-};
-
-__device__ __forceinline__ AxisTiles axis_tiles(int lo, int cnt, int n, int T, int nT) {
-    if (cnt <= 0) return {0, 0, 0};
-    if (cnt >= n) return {0, nT, nT};
-    const int s = imod(lo, n), e = s + cnt;
-    const int t0 = s / T;
-    if (e <= n) {
-        const int c = (e - 1) / T - t0 + 1;
-        return {t0, c, c};
-    }
-    const int t2 = (e - n - 1) / T;  // last tile of the segment wrapped to the start
-    if (t2 >= t0) return {0, nT, nT};  // both segments meet: every tile
-    return {t0, nT - t0, nT - t0 + t2 + 1};
-}
-
 // One CTA per leaf (apl consecutive atoms in bisection order): the atoms' boxes
 // and factor arrays; the leaf's box (structure C of Sec. 3.2.2: the box around
 // the cutoff boxes of the leaf's atoms, each shifted to the periodic image
@@ -110,103 +88,19 @@ __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int
     if (!bins) return;
     // one warp per atom appends it to its tiles' lists
     const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    for (int i = i0 + (int)(threadIdx.x >> 5); i < i1; i += nwarps) {
-        const AtomPrep<T> p = a.prep[i];
-        const AxisTiles ra = axis_tiles(p.lo[0], p.cnt[0], a.n1, TA, tA);
-        const AxisTiles rb = axis_tiles(p.lo[1], p.cnt[1], a.n2, TB, tB);
-        const AxisTiles rc = axis_tiles(p.lo[2], p.cnt[2], a.n3, TC, tC);
-        const int nbc = rb.count * rc.count;
-        const int tot = ra.count * nbc;
-        const int4 entry = make_int4(i, p.st[0] | (p.cnt[0] << 16), p.st[1] | (p.cnt[1] << 16),
-                                     p.st[2] | (p.cnt[2] << 16));
-        for (int k = lane; k < tot; k += 32) {
-            const int ka = k / nbc, r = k - ka * nbc, kb = r / rc.count, kc = r - kb * rc.count;
-            const int tile = (ra.tile(ka) * tB + rb.tile(kb)) * tC + rc.tile(kc);
-            const int slot = atomicAdd(cursor + tile, 1);
-            if (slot < kBinCap) list[(long long)tile * kBinCap + slot] = entry;
-        }
-    }
+    for (int i = i0 + (int)(threadIdx.x >> 5); i < i1; i += nwarps) bin_atom(a, i, tA, tB, tC, cursor, list, lane, 32);
 }
 
-// Splat of one tile from its bin: the list is sorted by atom index in shared
-// memory (a rank sort; indices in a list are distinct), so the summation order
-// is that of the leaf-selecting splat, then factors are staged in batches and
-// accumulated as there.  Longer lists take the leaf-selecting path.
 // Grid (tiles along c, b, a); FULL: every tile lies inside the grid (TA | N1, TB | N2, TC | N3).
 template <typename T, bool FULL>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 4)
     k_splat_binned(AtomArgs<T> a, T* __restrict__ rho, const int* __restrict__ cursor,
                    const int4* __restrict__ list) {
-    __shared__ int4 ent[kBinCap];
-    __shared__ int4 sorted[kBinCap];
-    __shared__ __align__(16) T fa[kBatch][TA];
-    __shared__ T fb[kBatch][TB], fc[kBatch][TC];
+    __shared__ __align__(16) unsigned char ws[splat_binned_ws<T>()];
     const int tiles_c = gridDim.x, tiles_b = gridDim.y;
-    const int tc = blockIdx.x, tb = blockIdx.y, ta = blockIdx.z;
-    const int tile = (ta * tiles_b + tb) * tiles_c + tc;
-    const int L = cursor[tile];
-    if (L > kBinCap) {
+    const int tile = (blockIdx.z * tiles_b + blockIdx.y) * tiles_c + blockIdx.x;
+    if (!splat_tile_binned<T, FULL>(a, rho, tiles_b, tiles_c, tile, cursor, list, ws))
         splat_tile(a, rho, tiles_b, tiles_c, tile);
-        return;
-    }
-    for (int e = threadIdx.x; e < L; e += kThreads) ent[e] = list[(long long)tile * kBinCap + e];
-    __syncthreads();
-    for (int e = threadIdx.x; e < L; e += kThreads) {
-        const int4 v = ent[e];
-        int r = 0;
-        for (int f = 0; f < L; ++f) r += ent[f].x < v.x;
-        sorted[r] = v;
-    }
-    const int a0 = ta * TA, b0 = tb * TB, c0 = tc * TC;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T acc[TA];
-#pragma unroll
-    for (int i = 0; i < TA; ++i) acc[i] = T(0);
-    for (int bb = 0; bb < L; bb += kBatch) {
-        const int nb = min(kBatch, L - bb);
-        __syncthreads();  // sorted[] complete / previous batch consumed
-        // factors: one global load per staged value (the entry carries the box), plus q n per c value
-        for (int e = threadIdx.x; e < nb * TC; e += kThreads) {
-            const int t = e / TC, k = e - t * TC;
-            const int4 E = sorted[bb + t];
-            const T sc = FULL || c0 + k < a.n3 ? image_sum(a.fac + ((long long)E.x * 3 + 2) * a.fb, c0 + k,
-                                                           E.w & 0xffff, E.w >> 16, a.n3)
-                                               : T(0);
-            const AtomPrep<T>& p = a.prep[E.x];
-            fc[t][k] = p.qn * sc + p.ql * sc;
-        }
-        for (int e = threadIdx.x; e < nb * TA; e += kThreads) {
-            const int t = e / TA, f = e - t * TA;
-            const int4 E = sorted[bb + t];
-            fa[t][f] = FULL || a0 + f < a.n1
-                           ? image_sum(a.fac + (long long)E.x * 3 * a.fb, a0 + f, E.y & 0xffff, E.y >> 16, a.n1)
-                           : T(0);
-        }
-        for (int e = threadIdx.x; e < nb * TB; e += kThreads) {
-            const int t = e / TB, f = e - t * TB;
-            const int4 E = sorted[bb + t];
-            fb[t][f] = FULL || b0 + f < a.n2 ? image_sum(a.fac + ((long long)E.x * 3 + 1) * a.fb, b0 + f,
-                                                         E.z & 0xffff, E.z >> 16, a.n2)
-                                             : T(0);
-        }
-        __syncthreads();
-        for (int t = 0; t < nb; ++t) {
-            const T s = fb[t][warp] * fc[t][lane];
-#pragma unroll
-            for (int i = 0; i < TA; ++i) acc[i] += fa[t][i] * s;
-        }
-    }
-    const int b = b0 + warp, c = c0 + lane;
-    const long long slice = (long long)a.n2 * a.n3;
-    T* out = rho + a0 * slice + (long long)b * a.n3 + c;
-    if (FULL) {
-#pragma unroll
-        for (int i = 0; i < TA; ++i) out[i * slice] = acc[i];
-    } else if (b < a.n2 && c < a.n3) {
-#pragma unroll
-        for (int i = 0; i < TA; ++i)
-            if (a0 + i < a.n1) out[i * slice] = acc[i];
-    }
 }
 
 // ---------------------------------------------------------------- forces

@@ -1,7 +1,7 @@
 // batch.cu -- many independent cells with uneven grids in one persistent launch.
 //
-// Each cell is a full Hartree step (atom preparation, splat, five Poisson
-// passes, E_H).  All cells' work is cut into items (stage, cell, tile) and put
+// Each cell is a full Hartree step (atom preparation with the splat tiles' atom
+// lists, the binned splat, five Poisson passes, E_H).  All cells' work is cut into items (stage, cell, tile) and put
 // in one global queue in stage-major order: every item of stage s (of every
 // cell) precedes every item of stage s + 1.  Persistent CTAs take items with
 // one atomic increment; before running an item of stage s of cell c, a CTA
@@ -12,6 +12,7 @@
 //
 // The launch is asynchronous, allocates nothing and can be captured in a
 // CUDA graph (two memsets and one kernel).
+#include <algorithm>
 #include <vector>
 
 #include "atoms_dev.cuh"
@@ -30,6 +31,9 @@ struct BatchCell {
     long long grid_off;  // first element of the cell's grid in the caller's vh
     int atom_off;        // first atom of the cell in the caller's pos / q
     int splat_tb, splat_tc;
+    int splat_ta;
+    int* cursor;         // the cell's splat-tile lists (its plan's): atoms per tile, then the entries
+    int4* list;
     double eh_factor;    // 2 pi Omega / N^2
     int cnt[NST];        // items of each stage
 };
@@ -115,13 +119,25 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batched(BatchArgs b, const d
             aa.q = q + cell.atom_off;
             float* grid = vh + cell.grid_off;
             switch (s) {
-                case ST_PREP: atom_prep_one(aa, t * kThreads + threadIdx.x); break;
-                case ST_FACT: atom_factors_one(aa, (long long)t * kThreads + threadIdx.x); break;
-                case ST_LEAF:
-                    leaf_box_one(aa.prep, aa.n, aa.apl, aa.nleaves, pa.n1, pa.n2, pa.n3, aa.leaf,
-                                 t * kThreads + threadIdx.x);
+                case ST_PREP:
+                    atom_prep_one(aa, t * kThreads + threadIdx.x);
+                    if (t == 0)  // empty lists for the leaf stage's appends
+                        for (int i = threadIdx.x; i < cell.splat_ta * cell.splat_tb * cell.splat_tc; i += kThreads)
+                            cell.cursor[i] = 0;
                     break;
-                case ST_SPLAT: splat_tile(aa, grid, cell.splat_tb, cell.splat_tc, t); break;
+                case ST_FACT: atom_factors_one(aa, (long long)t * kThreads + threadIdx.x); break;
+                case ST_LEAF: {
+                    const int i = t * kThreads + threadIdx.x;
+                    leaf_box_one(aa.prep, aa.n, aa.apl, aa.nleaves, pa.n1, pa.n2, pa.n3, aa.leaf, i);
+                    if (i < aa.n)
+                        bin_atom(aa, i, cell.splat_ta, cell.splat_tb, cell.splat_tc, cell.cursor, cell.list, 0, 1);
+                    break;
+                }
+                case ST_SPLAT:
+                    if (!splat_tile_binned<float, false>(aa, grid, cell.splat_tb, cell.splat_tc, t, cell.cursor,
+                                                         cell.list, smem_raw))
+                        splat_tile(aa, grid, cell.splat_tb, cell.splat_tc, t);
+                    break;
                 case ST_C: c_r2c_tile<float, true>(grid, pa, t, smem_raw); break;
                 case ST_B: b_tile<float, false, true>(pa, t, smem_raw); break;
                 case ST_A: a_green_tile<float, true>(pa, t, t, smem_raw, red); break;
@@ -235,10 +251,13 @@ extern "C" int hartree_batch_create(const hartree_desc* descs, const int* atom_c
         bc.splat_tb = (p.n[1] + TB - 1) / TB;
         bc.splat_tc = (p.n[2] + TC - 1) / TC;
         const int tA = (p.n[0] + TA - 1) / TA;
+        bc.splat_ta = tA;
+        bc.cursor = p.bin_cursor;
+        bc.list = p.bin_list;
         const long long nlines = (long long)p.n[0] * p.n[1];
-        bc.cnt[ST_PREP] = (n + kThreads - 1) / kThreads;
+        bc.cnt[ST_PREP] = std::max(1, (n + kThreads - 1) / kThreads);  // item 0 also empties the tile lists
         bc.cnt[ST_FACT] = (int)((3LL * n * runs + kThreads - 1) / kThreads);
-        bc.cnt[ST_LEAF] = (bc.aa.nleaves + kThreads - 1) / kThreads;
+        bc.cnt[ST_LEAF] = (std::max(bc.aa.nleaves, n) + kThreads - 1) / kThreads;  // leaf boxes and tile lists
         bc.cnt[ST_SPLAT] = tA * bc.splat_tb * bc.splat_tc;
         bc.cnt[ST_C] = (int)((nlines + p.c_lines - 1) / p.c_lines);
         bc.cnt[ST_B] = p.n[0] * bc.pa.b_chunks;
@@ -251,6 +270,7 @@ extern "C" int hartree_batch_create(const hartree_desc* descs, const int* atom_c
         size_t sm = p.smem_c;
         if (p.smem_b > sm) sm = p.smem_b;
         if (p.smem_a > sm) sm = p.smem_a;
+        if (sm < (size_t)splat_binned_ws<float>()) sm = splat_binned_ws<float>();
         if (sm > h.smem) h.smem = sm;
     }
     long long item = 0;
