@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace hartree {
 
 template <typename T>
@@ -41,6 +43,26 @@ template <typename T>
 __host__ __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<T> b) {
     return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
 }
+// Two FP32 lanes as one value (the .f32x2 add, mul and fma of sm_100-class GPUs): the butterflies
+// below, instantiated with T = f2x, transform two columns at once.  Negation flips the sign bits
+// (integer pipe) instead of multiplying by -1.
+struct f2x {
+    float2 v;
+    f2x() = default;
+    __device__ __forceinline__ explicit f2x(float2 x) : v(x) {}
+    __device__ __forceinline__ explicit f2x(double s) : v(make_float2((float)s, (float)s)) {}
+    __device__ __forceinline__ explicit f2x(int s) : v(make_float2((float)s, (float)s)) {}
+};
+__device__ __forceinline__ f2x operator+(f2x a, f2x b) { return f2x(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2x operator-(f2x a) {
+    return f2x(make_float2(__int_as_float(__float_as_int(a.v.x) ^ 0x80000000),
+                           __int_as_float(__float_as_int(a.v.y) ^ 0x80000000)));
+}
+// a - b as b (-1) + a: exact product, one rounding, the same result as a subtraction
+__device__ __forceinline__ f2x operator-(f2x a, f2x b) { return f2x(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ f2x operator*(f2x a, f2x b) { return f2x(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2x fma_t(f2x a, f2x b, f2x c) { return f2x(__ffma2_rn(a.v, b.v, c.v)); }
+
 template <typename T>
 __host__ __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) {
     return mk(a.re * s, a.im * s);
@@ -66,6 +88,10 @@ __host__ __device__ __forceinline__ T kmul(T x, double c) {
         const float hi = (float)c;
         const float lo = (float)(c - (double)hi);
         return fmaf(x, hi, x * lo);
+    } else if constexpr (std::is_same<T, f2x>::value && COMP) {
+        const float hi = (float)c;
+        const float lo = (float)(c - (double)hi);
+        return fma_t(x, T((double)hi), x * T((double)lo));
     } else {
         return x * (T)c;
     }

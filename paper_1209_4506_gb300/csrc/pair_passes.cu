@@ -192,13 +192,25 @@ __device__ __forceinline__ void pdft16(c2* v) {
     }
 }
 
+// The other radices (3, 5, 6, 7, 9, 10, 12) run the engine's butterflies on the paired type f2x.
 template <int R, bool INV, bool COMP>
 __device__ __forceinline__ void pdft(c2* v) {
-    static_assert(R == 2 || R == 4 || R == 8 || R == 16, "paired radix");
-    if constexpr (R == 2) pdft2<INV>(v);
-    if constexpr (R == 4) pdft4<INV>(v);
-    if constexpr (R == 8) pdft8<INV, COMP>(v);
-    if constexpr (R == 16) pdft16<INV, COMP>(v);
+    if constexpr (R == 2) {
+        pdft2<INV>(v);
+    } else if constexpr (R == 4) {
+        pdft4<INV>(v);
+    } else if constexpr (R == 8) {
+        pdft8<INV, COMP>(v);
+    } else if constexpr (R == 16) {
+        pdft16<INV, COMP>(v);
+    } else {
+        cpx<f2x> w[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[r] = mk(f2x(v[r].re), f2x(v[r].im));
+        dft<f2x, R, INV, COMP>(w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = c2{w[r].re.v, w[r].im.v};
+    }
 }
 
 // a w (forward, with the twiddle's remainder) or a conj(w) (inverse, rounded value only);
@@ -504,7 +516,9 @@ __global__ void __launch_bounds__(NT* G, MINB)
     constexpr int NBOX = N / BOXR;
     constexpr int TILE = N * COLS * 2;  // floats per tile buffer
     constexpr uint32_t TILE_BYTES = (uint32_t)N * COLS * 8;
-    constexpr int SH = COLS <= 8 ? ilog2(R0) : 0;  // row swizzle of the split layout (32- or 64-byte rows)
+    // row swizzle of the split layout (32- or 64-byte rows; power-of-two, mirrored outer radices)
+    constexpr bool POW2 = (R0 & (R0 - 1)) == 0;
+    constexpr int SH = COLS <= 8 && POW2 && (R2 > 1 ? R0 == R2 : R0 == R1) ? ilog2(R0) : 0;
     static_assert(COLS == 4 || COLS == 8 || COLS == 16, "tiles of 4, 8 or 16 columns");
     static_assert(SH == 0 || (R2 > 1 ? R0 == R2 : R0 == R1), "the row swizzle assumes mirrored radices");
     static_assert(PP == 0 || R2 > 1, "the ping-pong chain is written for three-stage transforms");
@@ -791,6 +805,8 @@ struct ColPairCfg {
 
 // Paired variants by line length: one group per CTA (one or two ring slots, several CTAs per
 // SM), or one CTA per SM of several groups sharing the tables, with or without work buffers.
+// Lengths that are not powers of two take 16-column tiles (128-byte rows: conflict-free without a
+// swizzle) or, for 840, unswizzled 8-column tiles, and their butterflies run on the paired type.
 template <class F>
 bool with_col_pair_cfg(int n, int variant, F&& f) {
     switch (n) {
@@ -801,6 +817,16 @@ bool with_col_pair_cfg(int n, int variant, F&& f) {
             else if (variant == 4) f(ColPairCfg<64, 8, 4, 8, 2, 4, 1, 8, 2>{});
             else if (variant == 5) f(ColPairCfg<64, 8, 4, 8, 2, 4, 1, 8, 3>{});
             else f(ColPairCfg<128, 8, 4, 8, 2, 8, 3>{});
+            return true;
+        case 360:  // 16-column tiles, one group of 480 threads: 60, 36 and 60 (or 36, 60, 60) butterflies
+            if (variant == 1) f(ColPairCfg<480, 10, 6, 6, 2, 16, 1, 1, 3>{});
+            else f(ColPairCfg<480, 6, 10, 6, 2, 16, 1, 1, 3>{});
+            return true;
+        case 420:  // 16-column tiles, one group of 576 threads: 42, 60 and 70 butterflies per column and stage
+            f(ColPairCfg<576, 10, 7, 6, 2, 16, 1, 1, 3>{});
+            return true;
+        case 840:  // 8-column tiles, 480 threads: 70, 84 and 120 butterflies per column and stage; one slot
+            f(ColPairCfg<480, 12, 10, 7, 1, 8, 1, 1, 1>{});
             return true;
         case 512:
             if (variant == 1) f(ColPairCfg<256, 8, 8, 8, 2, 8, 1, 3>{});
@@ -816,7 +842,14 @@ bool with_col_pair_cfg(int n, int variant, F&& f) {
 
 }  // namespace
 
-int col_pair_variants(int n) { return n == 512 || n == 256 ? 6 : 0; }
+int col_pair_variants(int n) {
+    switch (n) {
+        case 256: case 512: return 6;
+        case 360: return 2;
+        case 420: case 840: return 1;
+        default: return 0;
+    }
+}
 
 bool col_pair_available(const Plan& p, int axis) {
     return p.prec != HARTREE_FP64 && p.tma_ok && col_pair_variants(p.n[axis]) > 0;
