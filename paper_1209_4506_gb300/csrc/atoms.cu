@@ -91,16 +91,87 @@ __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int
     for (int i = i0 + (int)(threadIdx.x >> 5); i < i1; i += nwarps) bin_atom(a, i, tA, tB, tC, cursor, list, lane, 32);
 }
 
+// Splat of one tile from its bin: the list is sorted by atom index in shared
+// memory (a rank sort; indices in a list are distinct), so the summation order
+// is that of the leaf-selecting splat, then factors are staged in batches and
+// accumulated as there.  Longer lists take the leaf-selecting path.  The same
+// steps as splat_tile_binned (the batched form's), written out here over static
+// shared arrays: behind the function's pointers this kernel ran 5% slower.
 // Grid (tiles along c, b, a); FULL: every tile lies inside the grid (TA | N1, TB | N2, TC | N3).
 template <typename T, bool FULL>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 4)
     k_splat_binned(AtomArgs<T> a, T* __restrict__ rho, const int* __restrict__ cursor,
                    const int4* __restrict__ list) {
-    __shared__ __align__(16) unsigned char ws[splat_binned_ws<T>()];
+    __shared__ int4 ent[kBinCap];
+    __shared__ int4 sorted[kBinCap];
+    __shared__ __align__(16) T fa[kBatch][TA];
+    __shared__ T fb[kBatch][TB], fc[kBatch][TC];
     const int tiles_c = gridDim.x, tiles_b = gridDim.y;
-    const int tile = (blockIdx.z * tiles_b + blockIdx.y) * tiles_c + blockIdx.x;
-    if (!splat_tile_binned<T, FULL>(a, rho, tiles_b, tiles_c, tile, cursor, list, ws))
+    const int tc = blockIdx.x, tb = blockIdx.y, ta = blockIdx.z;
+    const int tile = (ta * tiles_b + tb) * tiles_c + tc;
+    const int L = cursor[tile];
+    if (L > kBinCap) {
         splat_tile(a, rho, tiles_b, tiles_c, tile);
+        return;
+    }
+    for (int e = threadIdx.x; e < L; e += kThreads) ent[e] = list[(long long)tile * kBinCap + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < L; e += kThreads) {
+        const int4 v = ent[e];
+        int r = 0;
+        for (int f = 0; f < L; ++f) r += ent[f].x < v.x;
+        sorted[r] = v;
+    }
+    const int a0 = ta * TA, b0 = tb * TB, c0 = tc * TC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T acc[TA];
+#pragma unroll
+    for (int i = 0; i < TA; ++i) acc[i] = T(0);
+    for (int bb = 0; bb < L; bb += kBatch) {
+        const int nb = min(kBatch, L - bb);
+        __syncthreads();  // sorted[] complete / previous batch consumed
+        // factors: one global load per staged value (the entry carries the box), plus q n per c value
+        for (int e = threadIdx.x; e < nb * TC; e += kThreads) {
+            const int t = e / TC, k = e - t * TC;
+            const int4 E = sorted[bb + t];
+            const T sc = FULL || c0 + k < a.n3 ? image_sum(a.fac + ((long long)E.x * 3 + 2) * a.fb, c0 + k,
+                                                           E.w & 0xffff, E.w >> 16, a.n3)
+                                               : T(0);
+            const AtomPrep<T>& p = a.prep[E.x];
+            fc[t][k] = p.qn * sc + p.ql * sc;
+        }
+        for (int e = threadIdx.x; e < nb * TA; e += kThreads) {
+            const int t = e / TA, f = e - t * TA;
+            const int4 E = sorted[bb + t];
+            fa[t][f] = FULL || a0 + f < a.n1
+                           ? image_sum(a.fac + (long long)E.x * 3 * a.fb, a0 + f, E.y & 0xffff, E.y >> 16, a.n1)
+                           : T(0);
+        }
+        for (int e = threadIdx.x; e < nb * TB; e += kThreads) {
+            const int t = e / TB, f = e - t * TB;
+            const int4 E = sorted[bb + t];
+            fb[t][f] = FULL || b0 + f < a.n2 ? image_sum(a.fac + ((long long)E.x * 3 + 1) * a.fb, b0 + f,
+                                                         E.z & 0xffff, E.z >> 16, a.n2)
+                                             : T(0);
+        }
+        __syncthreads();
+        for (int t = 0; t < nb; ++t) {
+            const T s = fb[t][warp] * fc[t][lane];
+#pragma unroll
+            for (int i = 0; i < TA; ++i) acc[i] += fa[t][i] * s;
+        }
+    }
+    const int b = b0 + warp, c = c0 + lane;
+    const long long slice = (long long)a.n2 * a.n3;
+    T* out = rho + a0 * slice + (long long)b * a.n3 + c;
+    if (FULL) {
+#pragma unroll
+        for (int i = 0; i < TA; ++i) out[i * slice] = acc[i];
+    } else if (b < a.n2 && c < a.n3) {
+#pragma unroll
+        for (int i = 0; i < TA; ++i)
+            if (a0 + i < a.n1) out[i * slice] = acc[i];
+    }
 }
 
 // ---------------------------------------------------------------- forces

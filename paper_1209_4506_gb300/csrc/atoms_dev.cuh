@@ -331,32 +331,34 @@ __device__ __forceinline__ void bin_atom(const AtomArgs<T>& a, int i, int tA, in
     }
 }
 
-// Splat of one tile from its bin: the list is sorted by atom index in shared
-// memory (a rank sort; indices in a list are distinct), so the summation order
-// is that of the leaf-selecting splat, then factors are staged in batches and
-// accumulated as there.  Returns false, having done nothing, when more than
+// Splat of one tile from its bin (the batched form's; k_splat_binned takes the
+// same steps): the list is sorted by atom index in shared memory (a rank sort;
+// indices in a list are distinct), so the summation order is that of the
+// leaf-selecting splat, then factors are staged in batches and accumulated as
+// there.  Returns false, having done nothing, when more than
 // kBinCap atoms reached the tile (the caller then takes the leaf-selecting
-// splat_tile).  ws: splat_binned_ws<T>() bytes of shared memory, 16-byte aligned.
-// FULL: every tile lies inside the grid (TA | N1, TB | N2, TC | N3).
+// splat_tile).  Shared memory: ent, sorted [kBinCap], fa [kBatch][TA] (16-byte
+// aligned), fb [kBatch][TB], fc [kBatch][TC] (SplatWs: the layout of one block).
+// FULL: every tile lies inside the grid (TA | N1, TB | N2, TC | N3).  CG: the lists were filled
+// earlier in the same launch (the batched form), so they are read through L2.
 template <typename T>
-__host__ __device__ constexpr int splat_binned_ws() {
-    return 2 * kBinCap * (int)sizeof(int4) + kBatch * (TA + TB + TC) * (int)sizeof(T);
-}
+struct SplatWs {
+    int4 ent[kBinCap], sorted[kBinCap];
+    T fa[kBatch][TA], fb[kBatch][TB], fc[kBatch][TC];
+};
 
-template <typename T, bool FULL>
-__device__ bool splat_tile_binned(const AtomArgs<T>& a, T* __restrict__ rho, int tiles_b, int tiles_c, int tile,
-                                  const int* __restrict__ cursor, const int4* __restrict__ list,
-                                  unsigned char* __restrict__ ws) {
-    int4* ent = reinterpret_cast<int4*>(ws);
-    int4* sorted = ent + kBinCap;
-    T(*fa)[TA] = reinterpret_cast<T(*)[TA]>(sorted + kBinCap);
-    T(*fb)[TB] = reinterpret_cast<T(*)[TB]>(fa + kBatch);
-    T(*fc)[TC] = reinterpret_cast<T(*)[TC]>(fb + kBatch);
+template <typename T, bool FULL, bool CG = false>
+__device__ __forceinline__ bool splat_tile_binned(const AtomArgs<T>& a, T* __restrict__ rho, int tiles_b, int tiles_c,
+                                                  int tile,
+                                  const int* __restrict__ cursor, const int4* __restrict__ list, int4* ent,
+                                  int4* sorted, T (*fa)[TA], T (*fb)[TB], T (*fc)[TC]) {
     const int tc = tile % tiles_c, tb = (tile / tiles_c) % tiles_b, ta = tile / (tiles_c * tiles_b);
-    // the lists may have been filled earlier in the same launch (the batched form): read through L2
-    const int L = __ldcg(cursor + tile);
+    const int L = CG ? __ldcg(cursor + tile) : cursor[tile];
     if (L > kBinCap) return false;
-    for (int e = threadIdx.x; e < L; e += kThreads) ent[e] = __ldcg(list + (long long)tile * kBinCap + e);
+    for (int e = threadIdx.x; e < L; e += kThreads) {
+        const int4* src = list + (long long)tile * kBinCap + e;
+        ent[e] = CG ? __ldcg(src) : *src;
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < L; e += kThreads) {
         const int4 v = ent[e];

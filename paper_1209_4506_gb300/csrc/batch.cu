@@ -133,11 +133,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batched(BatchArgs b, const d
                         bin_atom(aa, i, cell.splat_ta, cell.splat_tb, cell.splat_tc, cell.cursor, cell.list, 0, 1);
                     break;
                 }
-                case ST_SPLAT:
-                    if (!splat_tile_binned<float, false>(aa, grid, cell.splat_tb, cell.splat_tc, t, cell.cursor,
-                                                         cell.list, smem_raw))
+                case ST_SPLAT: {
+                    SplatWs<float>& w = *reinterpret_cast<SplatWs<float>*>(smem_raw);
+                    if (!splat_tile_binned<float, false, true>(aa, grid, cell.splat_tb, cell.splat_tc, t, cell.cursor,
+                                                         cell.list, w.ent, w.sorted, w.fa, w.fb, w.fc))
                         splat_tile(aa, grid, cell.splat_tb, cell.splat_tc, t);
                     break;
+                }
                 case ST_C: c_r2c_tile<float, true>(grid, pa, t, smem_raw); break;
                 case ST_B: b_tile<float, false, true>(pa, t, smem_raw); break;
                 case ST_A: a_green_tile<float, true>(pa, t, t, smem_raw, red); break;
@@ -270,7 +272,7 @@ extern "C" int hartree_batch_create(const hartree_desc* descs, const int* atom_c
         size_t sm = p.smem_c;
         if (p.smem_b > sm) sm = p.smem_b;
         if (p.smem_a > sm) sm = p.smem_a;
-        if (sm < (size_t)splat_binned_ws<float>()) sm = splat_binned_ws<float>();
+        if (sm < sizeof(SplatWs<float>)) sm = sizeof(SplatWs<float>);
         if (sm > h.smem) h.smem = sm;
     }
     long long item = 0;
