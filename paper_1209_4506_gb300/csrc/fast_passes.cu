@@ -34,6 +34,10 @@ __device__ __forceinline__ cpx<T> twmul(cpx<T> a, const TwPair<T>& w, bool inv) 
         const float tr = a.re * w.l.re - a.im * lo_im;
         const float ti = a.re * lo_im + a.im * w.l.re;
         return mk(fmaf(a.re, w.h.re, fmaf(-a.im, hi_im, tr)), fmaf(a.re, hi_im, fmaf(a.im, w.h.re, ti)));
+    } else if constexpr (std::is_same<T, f2x>::value && COMP) {
+        const T tr = a.re * w.l.re - a.im * lo_im;
+        const T ti = a.re * lo_im + a.im * w.l.re;
+        return mk(fma_t(a.re, w.h.re, fma_t(-a.im, hi_im, tr)), fma_t(a.re, hi_im, fma_t(a.im, w.h.re, ti)));
     } else {
         return mk(a.re * w.h.re - a.im * hi_im, a.re * hi_im + a.im * w.h.re);
     }
@@ -784,6 +788,213 @@ __global__ void __launch_bounds__(NT, MINB)
 }
 
 
+
+// ------------------------------------------------------------------ paired-lane streamed c passes (FP32)
+// The bulk-streamed c passes with every thread transforming one butterfly of two lines at once, as
+// the two lanes of the paired type f2x (radices of any kind): TPL threads per pair of lines, half
+// the threads of k_r2c_stream / k_c2r_stream for the same tile.  Same ring, tiles and arithmetic
+// (forward twiddles and constants compensated, inverse rounded), so the same results.
+__device__ __forceinline__ f2x dup2(float x) { return f2x(make_float2(x, x)); }
+__device__ __forceinline__ TwPair<f2x> pair_of(const TwPair<float>& w) {
+    return TwPair<f2x>{mk(dup2(w.h.re), dup2(w.h.im)), mk(dup2(w.l.re), dup2(w.l.im))};
+}
+__device__ __forceinline__ cpx<f2x> pair_of(cpx<float> w) { return mk(dup2(w.re), dup2(w.im)); }
+__device__ __forceinline__ cpx<f2x> lanes(cpx<float> x, cpx<float> y) {
+    return mk(f2x(make_float2(x.re, y.re)), f2x(make_float2(x.im, y.im)));
+}
+__device__ __forceinline__ cpx<float> lane0(cpx<f2x> v) { return mk(v.re.v.x, v.im.v.x); }
+__device__ __forceinline__ cpx<float> lane1(cpx<f2x> v) { return mk(v.re.v.y, v.im.v.y); }
+
+// Stage and post-processing twiddles of LineTwLayout on both lanes.
+template <int R0, int R1, int R2>
+__device__ __forceinline__ void fill_line_tw_fwd_pair(TwPair<f2x>* tw, const TwPair<float>* g) {
+    using L = LineTwLayout<R0, R1, R2>;
+    auto get = [&](int e) { return pair_of(g[e]); };
+    fill_stage_tw<L::M, R1, R0, 2>(tw, get);
+    if constexpr (R2 > 1) fill_stage_tw<L::M, R2, R0 * R1, 2>(tw + L::s2, get);
+    for (int k = threadIdx.x; k <= L::M / 2; k += blockDim.x) tw[L::s2 + L::s3 + k] = pair_of(g[k]);
+}
+template <int R0, int R1, int R2>
+__device__ __forceinline__ void fill_line_tw_inv_pair(cpx<f2x>* tw, const TwPair<float>* g) {
+    using L = LineTwLayout<R0, R1, R2>;
+    auto get = [&](int e) { return pair_of(g[e].h); };
+    fill_stage_tw<L::M, R1, R0, 2>(tw, get);
+    if constexpr (R2 > 1) fill_stage_tw<L::M, R2, R0 * R1, 2>(tw + L::s2, get);
+    for (int k = threadIdx.x; k < L::M; k += blockDim.x) tw[L::s2 + L::s3 + k] = pair_of(g[k].h);
+}
+
+struct LinePairSmem {  // a pair of lines, padded: point n of both at p[pidx(n)]
+    cpx<f2x>* p;
+    __device__ __forceinline__ cpx<f2x> ld_(int, int n) const { return p[pidx(n)]; }
+    __device__ __forceinline__ void st_(int, int n, cpx<f2x> v) const { p[pidx(n)] = v; }
+};
+
+struct LinePairRealIn {  // z[n] = rho[2n] + i rho[2n+1] of lines z and z + stride (a ring slot)
+    const cpx<float>* z;
+    int stride;
+    __device__ __forceinline__ cpx<f2x> ld_(int, int n) const { return lanes(z[n], z[stride + n]); }
+};
+
+// Z[k] = (X[k] + conj X[M-k]) + i w^-k (X[k] - conj X[M-k]) of rows x and x + stride (c2r pre-step)
+struct LinePairC2RIn {
+    const cpx<float>* x;
+    int stride;
+    const cpx<f2x>* tw;  // exp(-2 pi i k / N3), rounded
+    int M;
+    __device__ __forceinline__ cpx<f2x> ld_(int, int k) const {
+        const cpx<f2x> x1 = lanes(x[k], x[stride + k]);
+        const cpx<f2x> x2 = conjg(lanes(x[M - k], x[stride + M - k]));
+        const cpx<f2x> Ep = x1 + x2;
+        const cpx<f2x> Op = twmul<false>(x1 - x2, TwPair<f2x>{tw[k], mk(f2x(0), f2x(0))}, true);
+        return mk(Ep.re - Op.im, Ep.im + Op.re);
+    }
+};
+
+struct LinePairRealOut {  // lines z and z + stride of the real output, each only if it exists
+    cpx<float>* z;
+    int stride;
+    bool act_a, act_b;
+    __device__ __forceinline__ void st_(int, int n, cpx<f2x> v) const {
+        if (act_a) z[n] = lane0(v);
+        if (act_b) z[stride + n] = lane1(v);
+    }
+};
+
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_r2c_pair(const float* __restrict__ rho, FastArgs<float> a, int ntiles, int* err) {
+    constexpr int M = R0 * R1 * R2;
+    constexpr int TPL = NT / (LINES / 2);
+    constexpr int LDP = M + M / 16 + 1;
+    constexpr int SLOT = LINES * M;  // complex elements per ring slot
+    static_assert(LINES % 2 == 0 && NT % (LINES / 2) == 0, "pairs of lines");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cpx<float>* ring = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<f2x>* S = reinterpret_cast<cpx<f2x>*>(ring + NBUF * SLOT);
+    TwPair<f2x>* TW = reinterpret_cast<TwPair<f2x>*>(S + (LINES / 2) * LDP);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(TW + LineTwLayout<R0, R1, R2>::fwd);
+    fill_line_tw_fwd_pair<R0, R1, R2>(TW, a.twpc);
+    const TwPair<f2x>* TWP = TW + LineTwLayout<R0, R1, R2>::s2 + LineTwLayout<R0, R1, R2>::s3;
+    const long long nlines = (long long)a.n1 * a.n2;
+    auto issue = [&](int t, int b) {
+        const long long l0 = (long long)t * LINES;
+        const int nl = (int)min((long long)LINES, nlines - l0);
+        const uint32_t bytes = (uint32_t)nl * M * 8u;
+        mbar_arrive_expect_tx(&mbar[b], bytes);
+        bulk_load(ring + b * SLOT, rho + l0 * 2 * M, bytes, &mbar[b]);
+    };
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&mbar[b], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int b = 0; b < NBUF; ++b) {
+            const int t = blockIdx.x + b * gridDim.x;
+            if (t < ntiles) issue(t, b);
+        }
+    const int q = threadIdx.x / TPL, j0 = threadIdx.x % TPL;  // pair of lines 2q, 2q + 1
+    LinePairSmem sm{S + q * LDP};
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        const int b = k % NBUF;
+        const bool ok = mbar_wait(&mbar[b], (uint32_t)(k / NBUF) & 1u, err);
+        if (!__syncthreads_and(ok)) {
+            drain_ring<NBUF>(mbar, k, ntiles, err);
+            break;
+        }
+        const long long gline = (long long)t * LINES + 2 * q;
+        LinePairRealIn src{ring + b * SLOT + 2 * q * M, M};  // lines past the tile hold stale data
+        auto refill = [&] {
+            const int tn = t + NBUF * gridDim.x;
+            if (threadIdx.x == 0 && tn < ntiles) issue(tn, b);
+        };
+        line_ftransform<f2x, R0, R1, R2, TPL, false, true>(src, sm, sm, j0, static_cast<const TwPair<f2x>*>(TW),
+                                                             refill);
+        __syncthreads();
+        // X[k] and X[M - k] of both lines from one pair of loads, as in k_r2c_fast
+        if (gline < nlines) {
+            const bool act_b = gline + 1 < nlines;
+            cpx<float>* out = a.W + gline * a.ldc;
+            const f2x half = dup2(0.5f);
+            for (int kk = j0; kk <= M / 2; kk += TPL) {
+                const cpx<f2x> z1 = sm.ld_(0, kk);
+                const cpx<f2x> z2 = conjg(sm.ld_(0, kk == 0 ? 0 : M - kk));
+                const cpx<f2x> E = scale(z1 + z2, half);
+                const cpx<f2x> d = z1 - z2;
+                const cpx<f2x> O = mk(d.im * half, -(d.re * half));
+                const cpx<f2x> tq = twmul(O, TWP[kk], false);
+                const cpx<f2x> X1 = E + tq, X2 = conjg(E - tq);
+                out[kk] = lane0(X1);
+                out[M - kk] = lane0(X2);
+                if (act_b) {
+                    out[a.ldc + kk] = lane1(X1);
+                    out[a.ldc + M - kk] = lane1(X2);
+                }
+            }
+        }
+    }
+}
+
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_c2r_pair(float* __restrict__ vout, FastArgs<float> a, int ntiles, int* err) {
+    constexpr int M = R0 * R1 * R2;
+    constexpr int TPL = NT / (LINES / 2);
+    constexpr int LDP = M + M / 16 + 1;
+    static_assert(LINES % 2 == 0 && NT % (LINES / 2) == 0, "pairs of lines");
+    const int slot = LINES * a.ldc;  // complex elements per ring slot: LINES padded rows
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cpx<float>* ring = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<f2x>* S = reinterpret_cast<cpx<f2x>*>(ring + NBUF * slot);
+    cpx<f2x>* TWh = S + (LINES / 2) * LDP;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(TWh + LineTwLayout<R0, R1, R2>::inv);
+    fill_line_tw_inv_pair<R0, R1, R2>(TWh, a.twpc);
+    const cpx<f2x>* TWQ = TWh + LineTwLayout<R0, R1, R2>::s2 + LineTwLayout<R0, R1, R2>::s3;
+    const long long nlines = (long long)a.n1 * a.n2;
+    auto issue = [&](int t, int b) {
+        const long long l0 = (long long)t * LINES;
+        const int nl = (int)min((long long)LINES, nlines - l0);
+        const uint32_t bytes = (uint32_t)nl * (uint32_t)a.ldc * 8u;
+        mbar_arrive_expect_tx(&mbar[b], bytes);
+        bulk_load(ring + b * slot, a.W + l0 * a.ldc, bytes, &mbar[b]);
+    };
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&mbar[b], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int b = 0; b < NBUF; ++b) {
+            const int t = blockIdx.x + b * gridDim.x;
+            if (t < ntiles) issue(t, b);
+        }
+    const int q = threadIdx.x / TPL, j0 = threadIdx.x % TPL;
+    LinePairSmem sm{S + q * LDP};
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        const int b = k % NBUF;
+        const bool ok = mbar_wait(&mbar[b], (uint32_t)(k / NBUF) & 1u, err);
+        if (!__syncthreads_and(ok)) {
+            drain_ring<NBUF>(mbar, k, ntiles, err);
+            break;
+        }
+        const long long gline = (long long)t * LINES + 2 * q;
+        const bool act = gline < nlines;
+        LinePairC2RIn src{ring + b * slot + 2 * q * a.ldc, a.ldc, TWQ, M};
+        LinePairRealOut dst{reinterpret_cast<cpx<float>*>(vout + (act ? gline : 0) * a.n3), M, act,
+                            gline + 1 < nlines};
+        auto refill = [&] {
+            const int tn = t + NBUF * gridDim.x;
+            if (threadIdx.x == 0 && tn < ntiles) issue(tn, b);
+        };
+        line_ftransform<f2x, R0, R1, R2, TPL, true, true>(src, sm, dst, j0, static_cast<const cpx<f2x>*>(TWh),
+                                                            refill);
+    }
+}
+
 // ------------------------------------------------------------------ splat fused into the r2c pass (FP32)
 // The density never reaches HBM: persistent CTAs walk units of up to SEG tiles, a tile being LINES
 // consecutive c lines at one a index (b = b0 .. b0 + nl - 1), and compute each tile's density in
@@ -1092,32 +1303,42 @@ struct LineCfg {
 
 // Bulk-streamed c-pass configuration (FP32): LINES lines per tile, NBUF ring slots, MINB CTAs per SM
 // (fewer where they do not fit).
-template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB = 2>
+template <int LINES, int NT, int R0, int R1, int R2, int NBUF, int MINB = 2, bool PAIR = false>
 struct LineStreamCfg {
     static constexpr int lines = LINES, m = R0 * R1 * R2;
+    using E = std::conditional_t<PAIR, f2x, float>;  // element of the work buffer and the twiddle tables
     static size_t smem_work() { return (size_t)LINES * (m + m / 16 + 1) * sizeof(cpx<float>) + NBUF * 8; }
     static size_t smem_r2c() {
         return (size_t)NBUF * LINES * m * sizeof(cpx<float>) + smem_work() +
-               (size_t)LineTwLayout<R0, R1, R2>::fwd * sizeof(TwPair<float>);
+               (size_t)LineTwLayout<R0, R1, R2>::fwd * sizeof(TwPair<E>);
     }
     static size_t smem_c2r(int ldc) {
         return (size_t)NBUF * LINES * ldc * sizeof(cpx<float>) + smem_work() +
-               (size_t)LineTwLayout<R0, R1, R2>::inv * sizeof(cpx<float>);
+               (size_t)LineTwLayout<R0, R1, R2>::inv * sizeof(cpx<E>);
     }
     static size_t smem() { return 0; }  // checked per kernel in configure()
+    static auto r2c() {
+        if constexpr (PAIR)
+            return k_r2c_pair<LINES, NT, R0, R1, R2, NBUF, MINB>;
+        else
+            return k_r2c_stream<LINES, NT, R0, R1, R2, NBUF, MINB>;
+    }
+    static auto c2r() {
+        if constexpr (PAIR)
+            return k_c2r_pair<LINES, NT, R0, R1, R2, NBUF, MINB>;
+        else
+            return k_c2r_stream<LINES, NT, R0, R1, R2, NBUF, MINB>;
+    }
     static cudaError_t configure(int optin) {
         cudaError_t e;
-        if ((e = allow_max_dynamic_smem(k_r2c_stream<LINES, NT, R0, R1, R2, NBUF, MINB>, optin))) return e;
-        return allow_max_dynamic_smem(k_c2r_stream<LINES, NT, R0, R1, R2, NBUF, MINB>, optin);
+        if ((e = allow_max_dynamic_smem(r2c(), optin))) return e;
+        return allow_max_dynamic_smem(c2r(), optin);
     }
     // CTAs per SM the persistent grid relies on: MINB, or fewer if they do not fit
     static int resident(bool inverse, size_t need) {
         int b = 0;
-        const cudaError_t e =
-            inverse ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          &b, k_c2r_stream<LINES, NT, R0, R1, R2, NBUF, MINB>, NT, need)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          &b, k_r2c_stream<LINES, NT, R0, R1, R2, NBUF, MINB>, NT, need);
+        const cudaError_t e = inverse ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, c2r(), NT, need)
+                                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, r2c(), NT, need);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return 1;
@@ -1132,11 +1353,9 @@ struct LineStreamCfg {
         int grid = resident(inverse, need) * sm_count;
         if (grid > ntiles) grid = ntiles;
         if (!inverse)
-            k_r2c_stream<LINES, NT, R0, R1, R2, NBUF, MINB>
-                <<<grid, NT, need, s>>>(static_cast<const float*>(in), a, ntiles, err);
+            r2c()<<<grid, NT, need, s>>>(static_cast<const float*>(in), a, ntiles, err);
         else
-            k_c2r_stream<LINES, NT, R0, R1, R2, NBUF, MINB>
-                <<<grid, NT, need, s>>>(static_cast<float*>(out), a, ntiles, err);
+            c2r()<<<grid, NT, need, s>>>(static_cast<float*>(out), a, ntiles, err);
         return grid;
     }
 };
@@ -1152,13 +1371,29 @@ bool with_line_stream_cfg(int m, int variant, F&& f) {
             else f(LineStreamCfg<16, 256, 16, 16, 1, 2>{});
             return true;
         case 512: f(LineStreamCfg<8, 256, 8, 8, 8, 2>{}); return true;
-        case 200: f(LineStreamCfg<16, 256, 8, 5, 5, 2>{}); return true;
-        case 105: f(LineStreamCfg<16, 256, 3, 5, 7, 2>{}); return true;
-        case 210: f(LineStreamCfg<16, 256, 6, 5, 7, 2>{}); return true;
+        // mixed radices, variants 1, 2: each thread takes a butterfly of two lines (paired lanes)
+        case 200:
+            if (variant == 1) f(LineStreamCfg<16, 128, 8, 5, 5, 2, 3, true>{});
+            else if (variant == 2) f(LineStreamCfg<16, 128, 8, 5, 5, 1, 4, true>{});
+            else f(LineStreamCfg<16, 256, 8, 5, 5, 2>{});
+            return true;
+        case 105:
+            if (variant == 1) f(LineStreamCfg<16, 128, 3, 5, 7, 2, 3, true>{});
+            else if (variant == 2) f(LineStreamCfg<16, 128, 3, 5, 7, 1, 4, true>{});
+            else f(LineStreamCfg<16, 256, 3, 5, 7, 2>{});
+            return true;
+        case 210:
+            if (variant == 1) f(LineStreamCfg<16, 128, 6, 5, 7, 2, 3, true>{});
+            else if (variant == 2) f(LineStreamCfg<16, 128, 6, 5, 7, 1, 4, true>{});
+            else f(LineStreamCfg<16, 256, 6, 5, 7, 2>{});
+            return true;
         default: return false;
     }
 }
-int line_stream_variants(int m) { return m == 256 ? 2 : (with_line_stream_cfg(m, 0, [](auto) {}) ? 1 : 0); }
+int line_stream_variants(int m) {
+    if (m == 200 || m == 105 || m == 210) return 3;
+    return m == 256 ? 2 : (with_line_stream_cfg(m, 0, [](auto) {}) ? 1 : 0);
+}
 
 // TMA-streamed column pass configuration (FP32): COLS columns (16: 128-byte rows, one CTA per
 // SM; 8: 64-byte rows, MINB CTAs per SM, each with its own barriers) per tile.
