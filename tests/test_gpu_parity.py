@@ -345,7 +345,9 @@ def test_single_passes_reproduce_solve_density(precision):
 @pytest.mark.parametrize(
     "shape,precision",
     [((512, 256, 512), "fp32"), ((256, 512, 256), "fp32"), ((256, 512, 256), "fp64"), ((360, 384, 400), "fp32"),
-     ((420, 420, 210), "fp32"), ((840, 24, 420), "fp32"), ((840, 24, 420), "fp64")],
+     ((420, 420, 210), "fp32"), ((840, 24, 420), "fp32"), ((840, 24, 420), "fp64"),
+     # odd line counts (315 lines, M = 200 and 210): the paired c passes' last pair has one line
+     ((15, 21, 400), "fp32"), ((15, 21, 420), "fp32")],
 )
 def test_kernel_variants_agree(shape, precision):
     """Every compiled variant of every pass kind (tile shapes, thread counts, radix orders,
