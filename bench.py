@@ -353,13 +353,15 @@ def side_sections(args, plan, pos_h, q_h, pos, q, rho, vh, stream, world, barrie
     # end to end: pinned host buffers in, host results out, copies and read-back inside the timed region
     pos_pin = torch.tensor(pos_h).pin_memory()
     q_pin = torch.tensor(q_h).pin_memory()
+    eh_pin = torch.empty(1, dtype=torch.float64).pin_memory().numpy()
+    f_pin = torch.empty((len(q_h), 3), dtype=torch.float64).pin_memory().numpy()
     for _ in range(3):
-        plan.step_host(pos_pin.numpy(), q_pin.numpy())
+        plan.step_host(pos_pin.numpy(), q_pin.numpy(), eh_out=eh_pin, f_out=f_pin)
     n_e2e = max(10, min(args.steps, 100))
     barrier()
     t0 = time.perf_counter()
     for _ in range(n_e2e):
-        plan.step_host(pos_pin.numpy(), q_pin.numpy())
+        plan.step_host(pos_pin.numpy(), q_pin.numpy(), eh_out=eh_pin, f_out=f_pin)
     t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e = {"value": job_throughput(ybytes, n_e2e, t_e2e, world), "unit": "GB/s",
            "h2d_bytes_per_step": int(pos_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(8 + pos_h.nbytes),

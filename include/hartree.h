@@ -213,8 +213,13 @@ int hartree_step(hartree_plan plan, const double* pos, const double* q, int n, v
 /*
  * End-to-end step on host buffers: copies pos and q to the device, runs
  * splat, solve and forces with V_H kept in the plan's grid buffer, copies E_H
- * (and forces when f is not NULL) back, and waits for the stream.
+ * (and forces when f is not NULL) back, and waits for the work to finish.
+ * The work runs on a stream of the plan's own, after the work already queued
+ * on `stream`; its device part is captured into a CUDA graph on the first call
+ * and replayed while the atom count, the variant picks and the forces request
+ * stay the same (one launch instead of about ten).  Not thread-safe per plan.
  *   pos host [n][3], q host [n], eh host double out, f host [n][3] out or NULL.
+ * Returns HARTREE_ERR_NOT_CAPTURABLE when `stream` is being captured.
  */
 int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int n, double* eh, double* f,
                       void* stream);

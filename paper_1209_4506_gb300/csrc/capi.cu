@@ -134,6 +134,9 @@ void free_plan(Plan& p) {
                     p.d_err,       p.bin_cursor, p.bin_list, p.tc_dft, p.bisect, p.force_order};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (p.host_graph) cudaGraphExecDestroy(p.host_graph);
+    if (p.host_event) cudaEventDestroy(p.host_event);
+    if (p.host_stream) cudaStreamDestroy(p.host_stream);
 }
 
 bool finite_pos(double x) { return std::isfinite(x); }
@@ -559,6 +562,36 @@ int hartree_plan_autotune(hartree_plan plan, void* stream, int* choice) {
     return HARTREE_OK;
 }
 
+// The device work of hartree_step_host on the staged atoms: splat, solve, E_H, forces.
+static cudaError_t host_step_work(Plan& p, int n, bool forces, cudaStream_t s) {
+    cudaError_t e = launch_splat_solve(p, p.d_pos, p.d_q, n, p.R, p.d_eh, s);
+    if (e == cudaSuccess && forces) e = launch_forces(p, p.d_pos, p.d_q, n, p.R, p.d_f, nullptr, s, true);
+    return e;
+}
+
+// Capture host_step_work into p.host_graph (left null if the capture fails: the caller then
+// launches directly).  The plan's launch counter is advanced by the replays, not by the capture.
+static void capture_host_step(Plan& p, int n, bool forces, cudaStream_t s, const int* key) {
+    const unsigned long long l0 = p.launches;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const cudaError_t e = host_step_work(p, n, forces, s);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &g);
+    const unsigned long long l1 = p.launches;
+    p.launches = l0;
+    if (e == cudaSuccess && ec == cudaSuccess && g && cudaGraphInstantiate(&p.host_graph, g, 0) == cudaSuccess) {
+        p.host_graph_launches = l1 - l0;
+        for (int i = 0; i < 5; ++i) p.host_key[i] = key[i];
+    } else {
+        p.host_graph = nullptr;
+        cudaGetLastError();
+    }
+    if (g) cudaGraphDestroy(g);
+}
+
 int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int n, double* eh, double* f,
                       void* stream) {
     if (!plan || !eh || (n > 0 && (!pos || !q))) return fail(HARTREE_ERR_INVALID, "step_host: null argument");
@@ -573,16 +606,38 @@ int hartree_step_host(hartree_plan plan, const double* pos, const double* q, int
     if (e != cudaSuccess) return cuda_fail(e, "step_host");
     if (cap != cudaStreamCaptureStatusNone)
         return fail(HARTREE_ERR_NOT_CAPTURABLE, "step_host waits for the stream; it cannot be captured");
-    if (n > 0) {
-        e = cudaMemcpyAsync(p.d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(p.d_q, q, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    // the work runs on the plan's own stream (a capture needs a stream other than the legacy
+    // default one), after the caller's earlier work on `stream`; the call waits for it
+    if (!p.host_stream) {
+        e = cudaStreamCreateWithFlags(&p.host_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.host_event, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "step_host");
     }
-    if (e == cudaSuccess) e = launch_splat_solve(p, p.d_pos, p.d_q, n, p.R, p.d_eh, s);
-    if (e == cudaSuccess && f && n > 0) e = launch_forces(p, p.d_pos, p.d_q, n, p.R, p.d_f, nullptr, s, true);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(eh, p.d_eh, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && f && n > 0)
-        e = cudaMemcpyAsync(f, p.d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const cudaStream_t hs = p.host_stream;
+    e = cudaEventRecord(p.host_event, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, p.host_event, 0);
+    if (e == cudaSuccess && n > 0) {
+        e = cudaMemcpyAsync(p.d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, hs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p.d_q, q, sizeof(double) * n, cudaMemcpyHostToDevice, hs);
+    }
+    const bool forces = f && n > 0;
+    const int key[5] = {n, p.var[0], p.var[1], p.var[2], forces ? 1 : 0};
+    if (e == cudaSuccess && (!p.host_graph || !std::equal(key, key + 5, p.host_key))) {
+        if (p.host_graph) cudaGraphExecDestroy(p.host_graph);
+        p.host_graph = nullptr;
+        capture_host_step(p, n, forces, hs, key);
+    }
+    if (e == cudaSuccess) {
+        if (p.host_graph) {
+            e = cudaGraphLaunch(p.host_graph, hs);
+            p.launches += p.host_graph_launches;
+        } else {
+            e = host_step_work(p, n, forces, hs);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(eh, p.d_eh, sizeof(double), cudaMemcpyDeviceToHost, hs);
+    if (e == cudaSuccess && forces) e = cudaMemcpyAsync(f, p.d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, hs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(hs);
     return e == cudaSuccess ? HARTREE_OK : cuda_fail(e, "step_host");
 }
 

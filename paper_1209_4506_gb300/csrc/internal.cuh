@@ -175,6 +175,13 @@ struct Plan {
     double* d_q = nullptr;
     double* d_f = nullptr;
     double* d_eh = nullptr;
+    // hartree_step_host: its device work captured into a CUDA graph on a stream of the plan's own
+    // and replayed while the key (atom count, variant picks, forces wanted) stays the same
+    cudaStream_t host_stream = nullptr;
+    cudaEvent_t host_event = nullptr;
+    cudaGraphExec_t host_graph = nullptr;
+    int host_key[5] = {-1, -1, -1, -1, -1};
+    unsigned long long host_graph_launches = 0;
     size_t bytes = 0;
     // tiling
     int c_lines, b_cols, a_cols;

@@ -223,13 +223,18 @@ class HartreePlan:
     def launch_count(self) -> int:
         return int(capi.hartree_plan_launch_count(self.handle))
 
-    def step_host(self, pos: np.ndarray, q: np.ndarray, forces: bool = True):
-        """Host arrays in, (E_H, F or None) out; copies and waits inside the library."""
+    def step_host(self, pos: np.ndarray, q: np.ndarray, forces: bool = True, eh_out=None, f_out=None):
+        """Host arrays in, (E_H, F or None) out; copies and waits inside the library.  eh_out ([1]) and
+        f_out ([n][3]), float64 and C-contiguous, receive the results if given (pinned arrays make
+        the read-back a direct copy)."""
         pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
         q = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
         n = q.size
-        eh = np.zeros(1, dtype=np.float64)
-        f = np.empty((n, 3), dtype=np.float64) if forces else None
+        for name, arr, shape in (("eh_out", eh_out, (1,)), ("f_out", f_out, (n, 3))):
+            if arr is not None and (arr.dtype != np.float64 or arr.shape != shape or not arr.flags.c_contiguous):
+                raise ValueError(f"{name} must be a C-contiguous float64 array of shape {shape}")
+        eh = eh_out if eh_out is not None else np.zeros(1, dtype=np.float64)
+        f = (f_out if f_out is not None else np.empty((n, 3), dtype=np.float64)) if forces else None
         capi.check(capi.hartree_step_host(self.handle, pos.ctypes.data, q.ctypes.data, n, eh.ctypes.data,
                                           f.ctypes.data if forces else None, _stream_handle(self.device)))
         return float(eh[0]), f

@@ -293,6 +293,37 @@ def test_step_host_end_to_end():
     eh, f = plan.step_host(S.pos, S.q)
     assert abs(eh - ref["eh"]) <= TOL["fp32"]["e"] * abs(ref["eh"])
     assert np.max(np.abs(f - ref["forces"])) <= TOL["fp32"]["f"]
+    # the same into caller-owned (here pinned) output arrays
+    eh_out = torch.empty(1, dtype=torch.float64).pin_memory().numpy()
+    f_out = torch.empty((S.n_atoms, 3), dtype=torch.float64).pin_memory().numpy()
+    eh2, f2 = plan.step_host(S.pos, S.q, eh_out=eh_out, f_out=f_out)
+    assert f2 is f_out and eh2 == eh and np.array_equal(f2, f)
+    with pytest.raises(ValueError):
+        plan.step_host(S.pos, S.q, f_out=np.empty((S.n_atoms, 2)))
+
+
+def test_step_host_graph_follows_counts_variants_and_forces():
+    """hartree_step_host replays a captured graph: a new atom count, new variant picks or a call
+    without forces must capture again, and every replay must match the device step."""
+    S = synth.config2()
+    plan = HartreePlan(S.n, S.cell, S.sigma, "fp32", max_atoms=S.n_atoms)
+    pos, q = S.pos[:40], S.q[:40] - S.q[:40].mean()
+    for _ in range(2):
+        eh_a, f_a = plan.step_host(S.pos, S.q)
+        eh_b, f_b = plan.step_host(pos, q)
+    _, eh_d, f_d = plan.step(dev(pos), dev(q))
+    torch.cuda.synchronize()
+    assert eh_b == eh_d.item() and np.array_equal(f_b, f_d.cpu().numpy())
+    n0 = plan.launch_count
+    plan.step_host(pos, q)
+    per_call = plan.launch_count - n0
+    assert per_call > 1  # the replay counts the graph's kernels
+    eh_c, f_c = plan.step_host(pos, q, forces=False)
+    assert f_c is None and eh_c == eh_b
+    plan.set_variants([0, 0, 0])
+    eh_e, f_e = plan.step_host(pos, q)
+    assert abs(eh_e - eh_b) <= 1e-6 * abs(eh_b) and np.max(np.abs(f_e - f_b)) <= 1e-5
+    plan.close()
 
 
 def test_too_many_atoms_is_rejected():
