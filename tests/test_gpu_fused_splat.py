@@ -161,6 +161,19 @@ def test_fused_dense_tiles_span_several_batches_and_leaf_rounds(n_atoms):
     check_oracle(g, ref)
 
 
+def test_fused_pass_needs_the_flag():
+    """hartree_splat_pass refuses plans that do not use the fused kernel: no flag, or FP64."""
+    S = synth.config2()
+    P, Q = dev(S.pos), dev(S.q)
+    for precision, flags in (("fp32", 0), ("fp64", FUSED)):
+        plan = HartreePlan(S.n, S.cell, S.sigma, precision, flags=flags)
+        assert not plan.fused_splat
+        with pytest.raises(capi.HartreeError) as ei:
+            plan.splat_pass(P, Q)
+        assert ei.value.status == capi.HARTREE_ERR_UNSUPPORTED_SIZE
+        plan.close()
+
+
 def test_fused_no_atoms():
     S = synth.config2()
     plan = HartreePlan(S.n, S.cell, S.sigma, "fp32", flags=FUSED)
