@@ -47,13 +47,49 @@ __device__ __forceinline__ void atom_prep_one(const AtomArgs<T>& a, int i) {
     a.prep[i] = p;
 }
 
-// One thread per (atom, axis, run of kRun<T>() box points): fac / dfac computed in
-// FP64.  FP32 plans start each run with three exponentials and continue with
-// the exact ratio recurrence; FP64 plans evaluate every point directly.  The
-// recurrence's relative error after m steps is about m^2 / 2 FP64 roundings
-// (2e-13 at m = 64), far below the single FP32 rounding of each value, so FP32
-// runs are long: FP64 arithmetic runs at a small fraction of the FP32 rate, and
-// the exponentials dominate the setup.
+// Float-float numbers: the unevaluated sum hi + lo of two FP32 values with
+// |lo| <= ulp(hi) / 2, about 44 significant bits (Dekker's double-length
+// arithmetic: an FMA gives the exact error of a product, Knuth's two-sum that
+// of a sum).  The _rn intrinsics keep the compiler from contracting the steps.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_of(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+// a * b to float-float (the lo * lo term, 2^-48 relative, is dropped)
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.hi, b.hi, -p)));
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+// a * b rounded once to FP32 (up to the 2^-44 error of the operands)
+__device__ __forceinline__ float ff_mul_round(FF a, FF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    return __fadd_rn(p, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.hi, b.hi, -p))));
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bv = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));  // s + e = a.hi + b.hi exactly
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float t = __fadd_rn(s, e);
+    return {t, __fsub_rn(e, __fsub_rn(t, s))};
+}
+
+// One thread per (atom, axis, run of kRun<T>() box points).  FP64 plans evaluate
+// every point directly in FP64.  FP32 plans start each run with three FP64
+// exponentials and continue with the exact ratio recurrence in float-float: FP64
+// arithmetic runs at 1/64 of the FP32 rate on GB300, and a recurrence in FP64 made
+// the setup FP64-bound.  The recurrence's relative error after m steps is about
+// m^2 / 2 float-float roundings (3e-11 at m = 64), far below the single FP32
+// rounding of each stored value, so FP32 runs are long and the exponentials few.
 template <typename T>
 __host__ __device__ constexpr int kRun() {
     return sizeof(T) == 4 ? 64 : 8;
@@ -83,17 +119,20 @@ __device__ __forceinline__ void atom_factors_one(const AtomArgs<T>& a, long long
             df[m] = dm * g;
         }
     } else {
-        // exponent(m) = -(D0 + m h)^2 / s^2: successive ratios are exp(-(2 d_m h + h^2) / s^2)
+        // exponent(m) = -(D0 + m h)^2 / s^2: successive ratios are exp(-(2 d_m h + h^2) / s^2),
+        // and those ratios fall by the constant factor exp(-2 h^2 / s^2)
         const double ds = fma((double)m0, h, D0);
-        double g = exp(-ds * ds * a.inv_s2);
-        double r = exp(-(2.0 * ds * h + h * h) * a.inv_s2);
-        const double q = exp(-2.0 * h * h * a.inv_s2);
+        FF g = ff_of(exp(-ds * ds * a.inv_s2));
+        FF r = ff_of(exp(-(2.0 * ds * h + h * h) * a.inv_s2));
+        const FF q = ff_of(exp(-2.0 * h * h * a.inv_s2));
+        FF dm = ff_of(ds);
+        const FF hf = ff_of(h);
         for (int m = m0; m < m1; ++m) {
-            const double dm = fma((double)m, h, D0);
-            f[m] = (T)g;
-            df[m] = (T)(dm * g);
-            g *= r;
-            r *= q;
+            f[m] = g.hi;  // hi is the FP32 rounding of hi + lo
+            df[m] = ff_mul_round(dm, g);
+            g = ff_mul(g, r);
+            r = ff_mul(r, q);
+            dm = ff_add(dm, hf);
         }
     }
 }

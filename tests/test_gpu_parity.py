@@ -279,6 +279,36 @@ def test_fp32_factor_runs_longer_than_one_recurrence():
     assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("n,cell,sigma", [
+    ((48, 40, 56), (9.0, 8.5, 10.0), 0.7),     # 37-39 box points per axis: one FP32 run
+    ((112, 112, 120), (7.0, 7.0, 7.5), 0.6),   # 96-97 box points per axis: two FP32 runs
+])
+def test_single_atom_density_is_a_few_roundings_from_the_gaussian(n, cell, sigma, precision):
+    """One atom: inside its cutoff sphere rho = q n fa fb fc, each 1D factor the working-precision
+    rounding of exp(-d^2/s^2).  Against the oracle's FP64 Gaussian the FP32 error is then at most
+    7 roundings (three factors, q n times the c factor, two products), bar 8 u = 2^-21; a factor
+    recurrence that drifted by one rounding per box point would miss it by far.  Box points
+    outside the sphere (the oracle's cutoff is spherical) stay below e^-25 q n."""
+    rc = 5.0
+    rng = np.random.default_rng(sum(n))
+    pos = (rng.random((1, 3)) * np.array(cell))
+    q = np.array([1.3])
+    ref = O.splat(n, cell, sigma, pos, q, rc_sigmas=rc)
+    plan = HartreePlan(n, cell, sigma, precision, cutoff_sigmas=rc)
+    rho = plan.splat(dev(pos), dev(q))
+    torch.cuda.synchronize()
+    plan.device_status()
+    g = rho.double().cpu().numpy()
+    plan.close()
+    inside = ref != 0.0
+    bar = 2.0 ** -21 if precision == "fp32" else 1e-13
+    assert inside.sum() > 1000
+    assert np.max(np.abs(g[inside] - ref[inside]) / ref[inside]) <= bar
+    qn = q[0] * (np.pi * sigma * sigma) ** -1.5
+    assert np.max(np.abs(g[~inside])) <= np.exp(-rc * rc) * qn * (1 + 1e-5)
+
+
 def test_forces_recompute_when_vh_is_null():
     S, ref = oracle_cfg("cfg2")
     plan = HartreePlan(S.n, S.cell, S.sigma, "fp32")
