@@ -10,10 +10,11 @@
 // index lo_d + m at offset d_m = (lo_d + m) h_d - X_d, and
 //   fac[m] = exp(-d_m^2/s^2),  dfac[m] = d_m exp(-d_m^2/s^2).
 // k_leaf_setup runs one CTA per leaf of `apl` consecutive atoms: it finds each
-// atom's box and fills its factor arrays once per call in FP64 (three
-// exponentials per run of 8 box points, then the exact ratio recurrence
-// f_{m+1} = f_m r_m, r_{m+1} = r_m exp(-2 h^2/s^2)), rounding each value once,
-// so the FP32 splat and gather carry no exponential rounding bias.  It then
+// atom's box and fills its factor arrays once per call, each value rounded once
+// to the working precision, so the FP32 splat and gather carry no exponential
+// rounding bias (FP64 plans: an FP64 exponential per point; FP32 plans: two FP64
+// exponentials per run of up to 64 points, then the exact ratio recurrence
+// f_{m+1} = f_m r_m, r_{m+1} = r_m exp(-2 h^2/s^2) in float-float).  It then
 // builds the leaf's box (structure C of Sec. 3.2.2: the parallelepiped around
 // the basis spheres of the atoms one process holds) and lists each atom in every
 // splat tile its box reaches.  In the order of the modified recursive bisection
@@ -51,7 +52,11 @@ namespace {
 // further lookup.  Slots are taken with atomics, so a list is unordered (the
 // splat sorts it); a tile reached by more than kBinCap atoms keeps counting and
 // the splat then selects its atoms from the leaf boxes instead.
-constexpr int kSetupThreads = 512;  // one warp per atom of a leaf (16 atoms per leaf by default)
+// One thread per (atom, axis) finds that axis's box and goes straight on to the
+// factors of its first run, so the FP64 divisions and exponentials of the three
+// axes run side by side; 128-thread CTAs let several leaves share an SM and
+// cover each other's FP64 latency.
+constexpr int kSetupThreads = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int tA, int tB, int tC,
@@ -60,15 +65,37 @@ __global__ void __launch_bounds__(kSetupThreads) k_leaf_setup(AtomArgs<T> a, int
     __shared__ int bmin[3], bmax[3];
     const int l = blockIdx.x;
     const int i0 = l * a.apl, i1 = min(a.n, i0 + a.apl);
-    for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) atom_prep_one(a, i);
+    const int na = i1 - i0;
     if (threadIdx.x < 3) {
         bmin[threadIdx.x] = INT_MAX;
         bmax[threadIdx.x] = INT_MIN;
     }
+    for (int t = threadIdx.x; t < 3 * na; t += blockDim.x) {
+        const int i = i0 + t / 3, d = t - (t / 3) * 3;
+        const AxisBox b = atom_axis_box(a, i, d);
+        AtomPrep<T>& p = a.prep[i];
+        const T dh = (T)b.D0, dl = (T)(b.D0 - (double)dh);
+        p.lo[d] = b.lo;
+        p.st[d] = b.st;
+        p.cnt[d] = b.cnt;
+        p.dh[d] = dh;
+        p.dl[d] = dl;
+        if (d == 0) {
+            const double qn = a.q[i] * a.norm;
+            p.qn = (T)qn;
+            p.ql = (T)(qn - (double)p.qn);
+        }
+        atom_factors_run(a, i, d, 0, b.cnt, (double)dh + (double)dl);
+    }
     __syncthreads();  // the boxes are visible to the whole CTA
-    const int runs = (a.fb + kRun<T>() - 1) / kRun<T>();
-    const int ntask = (i1 - i0) * 3 * runs;
-    for (int t = threadIdx.x; t < ntask; t += blockDim.x) atom_factors_one(a, (long long)i0 * 3 * runs + t);
+    // the later runs of boxes longer than one run
+    const int later = (a.fb + kRun<T>() - 1) / kRun<T>() - 1;
+    for (int t = threadIdx.x; t < na * 3 * later; t += blockDim.x) {
+        const int i = i0 + t / (3 * later), rem = t - (t / (3 * later)) * 3 * later;
+        const int d = rem / later, run = 1 + rem - d * later;
+        const AtomPrep<T>& p = a.prep[i];
+        atom_factors_run(a, i, d, run * kRun<T>(), p.cnt[d], (double)p.dh[d] + (double)p.dl[d]);
+    }
     const int ns[3] = {a.n1, a.n2, a.n3};
     for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x)
         for (int d = 0; d < 3; ++d) {

@@ -23,23 +23,41 @@ __device__ __forceinline__ bool range_hits(int s, int len, int t0, int tn, int n
     return delta < len || delta + tn > n;
 }
 
+// The box of atom i along axis d: the grid points within rc of the atom's position X (wrapped
+// into the cell: any image gives the same periodic sum), from the unwrapped index lo, cnt of them
+// (at most fb), starting at the wrapped index st, and the offset D0 = lo h - X of the first.
+struct AxisBox {
+    int lo, cnt, st;
+    double D0;
+};
+
+template <typename T>
+__device__ __forceinline__ AxisBox atom_axis_box(const AtomArgs<T>& a, int i, int d) {
+    const double h = d == 0 ? a.h1 : (d == 1 ? a.h2 : a.h3);
+    const double L = d == 0 ? a.L1 : (d == 1 ? a.L2 : a.L3);
+    double X = a.pos[3 * i + d];
+    X -= L * floor(X / L);
+    const double lo = ceil((X - a.rc) / h);
+    const double hi = floor((X + a.rc) / h);
+    AxisBox b;
+    b.lo = (int)lo;
+    b.st = imod(b.lo, d == 0 ? a.n1 : (d == 1 ? a.n2 : a.n3));
+    b.cnt = hi >= lo ? min((int)(hi - lo) + 1, a.fb) : 0;
+    b.D0 = lo * h - X;
+    return b;
+}
+
 template <typename T>
 __device__ __forceinline__ void atom_prep_one(const AtomArgs<T>& a, int i) {
     if (i >= a.n) return;
-    const double hs[3] = {a.h1, a.h2, a.h3};
-    const double Ls[3] = {a.L1, a.L2, a.L3};
     AtomPrep<T> p;
     for (int d = 0; d < 3; ++d) {
-        double X = a.pos[3 * i + d];
-        X -= Ls[d] * floor(X / Ls[d]);  // any image of the atom gives the same periodic sum
-        const double lo = ceil((X - a.rc) / hs[d]);
-        const double hi = floor((X + a.rc) / hs[d]);
-        p.lo[d] = (int)lo;
-        p.st[d] = imod(p.lo[d], d == 0 ? a.n1 : (d == 1 ? a.n2 : a.n3));
-        p.cnt[d] = hi >= lo ? min((int)(hi - lo) + 1, a.fb) : 0;
-        const double D0 = lo * hs[d] - X;
-        p.dh[d] = (T)D0;
-        p.dl[d] = (T)(D0 - (double)p.dh[d]);
+        const AxisBox b = atom_axis_box(a, i, d);
+        p.lo[d] = b.lo;
+        p.st[d] = b.st;
+        p.cnt[d] = b.cnt;
+        p.dh[d] = (T)b.D0;
+        p.dl[d] = (T)(b.D0 - (double)p.dh[d]);
     }
     const double qn = a.q[i] * a.norm;
     p.qn = (T)qn;
@@ -95,20 +113,14 @@ __host__ __device__ constexpr int kRun() {
     return sizeof(T) == 4 ? 64 : 8;
 }
 
+// The factors of box points m0 .. min(cnt, m0 + kRun) - 1 of atom i along axis d, whose box
+// has cnt points from the offset D0 = lo h - X.
 template <typename T>
-__device__ __forceinline__ void atom_factors_one(const AtomArgs<T>& a, long long t) {
+__device__ __forceinline__ void atom_factors_run(const AtomArgs<T>& a, int i, int d, int m0, int cnt, double D0) {
     constexpr int kRun = hartree::kRun<T>();
-    const int runs = (a.fb + kRun - 1) / kRun;
-    if (t >= 3LL * a.n * runs) return;
-    const int i = (int)(t / (3 * runs));
-    const int rem = (int)(t - (long long)i * 3 * runs);
-    const int d = rem / runs, m0 = (rem - d * runs) * kRun;
-    const AtomPrep<T> p = a.prep[i];
-    const int cnt = p.cnt[d];
     if (m0 >= cnt) return;
     const int m1 = min(cnt, m0 + kRun);
     const double h = d == 0 ? a.h1 : (d == 1 ? a.h2 : a.h3);
-    const double D0 = (double)p.dh[d] + (double)p.dl[d];  // lo h - X
     T* f = a.fac + ((long long)i * 3 + d) * a.fb;
     T* df = a.dfac + ((long long)i * 3 + d) * a.fb;
     if constexpr (sizeof(T) == 8) {
@@ -124,7 +136,7 @@ __device__ __forceinline__ void atom_factors_one(const AtomArgs<T>& a, long long
         const double ds = fma((double)m0, h, D0);
         FF g = ff_of(exp(-ds * ds * a.inv_s2));
         FF r = ff_of(exp(-(2.0 * ds * h + h * h) * a.inv_s2));
-        const FF q = ff_of(exp(-2.0 * h * h * a.inv_s2));
+        const FF q = ff_of(a.qr[d]);
         FF dm = ff_of(ds);
         const FF hf = ff_of(h);
         for (int m = m0; m < m1; ++m) {
@@ -135,6 +147,19 @@ __device__ __forceinline__ void atom_factors_one(const AtomArgs<T>& a, long long
             dm = ff_add(dm, hf);
         }
     }
+}
+
+// One thread per (atom, axis, run of kRun<T>() box points), the box read from prep.
+template <typename T>
+__device__ __forceinline__ void atom_factors_one(const AtomArgs<T>& a, long long t) {
+    constexpr int kRun = hartree::kRun<T>();
+    const int runs = (a.fb + kRun - 1) / kRun;
+    if (t >= 3LL * a.n * runs) return;
+    const int i = (int)(t / (3 * runs));
+    const int rem = (int)(t - (long long)i * 3 * runs);
+    const int d = rem / runs, m0 = (rem - d * runs) * kRun;
+    const AtomPrep<T>& p = a.prep[i];
+    atom_factors_run(a, i, d, m0, p.cnt[d], (double)p.dh[d] + (double)p.dl[d]);
 }
 
 template <typename T>
@@ -307,6 +332,7 @@ inline AtomArgs<T> make_atom_args(const Plan& p, const double* pos, const double
     a.L3 = p.L[2];
     a.rc = p.rc;
     a.inv_s2 = 1.0 / (p.sigma * p.sigma);
+    for (int d = 0; d < 3; ++d) a.qr[d] = exp(-2.0 * p.h[d] * p.h[d] * a.inv_s2);
     a.is2h = (T)a.inv_s2;
     a.is2l = (T)(a.inv_s2 - (double)a.is2h);
     a.norm = pow(3.14159265358979323846 * p.sigma * p.sigma, -1.5);

@@ -130,6 +130,7 @@ struct AtomArgs {
     double L1, L2, L3;
     double rc;      // per-axis truncation radius (Bohr)
     double inv_s2;  // 1 / sigma^2
+    double qr[3];   // exp(-2 h^2 / s^2) per axis: the factor by which successive box ratios fall
     T is2h, is2l;   // 1 / sigma^2 split into high and low parts
     double norm;    // (pi sigma^2)^(-3/2)
     double dV;
