@@ -136,7 +136,7 @@ __device__ __forceinline__ void atom_factors_run(const AtomArgs<T>& a, int i, in
         const double ds = fma((double)m0, h, D0);
         FF g = ff_of(exp(-ds * ds * a.inv_s2));
         FF r = ff_of(exp(-(2.0 * ds * h + h * h) * a.inv_s2));
-        const FF q = ff_of(a.qr[d]);
+        const FF q = ff_of(d == 0 ? a.qr[0] : (d == 1 ? a.qr[1] : a.qr[2]));  // constant indices: a stays in registers
         FF dm = ff_of(ds);
         const FF hf = ff_of(h);
         for (int m = m0; m < m1; ++m) {
