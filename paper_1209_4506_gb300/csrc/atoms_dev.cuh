@@ -102,8 +102,9 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
 }
 
 // One thread per (atom, axis, run of kRun<T>() box points).  FP64 plans evaluate
-// every point directly in FP64.  FP32 plans start each run with three FP64
-// exponentials and continue with the exact ratio recurrence in float-float: FP64
+// every point directly in FP64.  FP32 plans start each run with two FP64
+// exponentials (the ratios' constant decay exp(-2 h^2 / s^2) is formed on the host)
+// and continue with the exact ratio recurrence in float-float: FP64
 // arithmetic runs at 1/64 of the FP32 rate on GB300, and a recurrence in FP64 made
 // the setup FP64-bound.  The recurrence's relative error after m steps is about
 // m^2 / 2 float-float roundings (3e-11 at m = 64), far below the single FP32

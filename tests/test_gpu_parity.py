@@ -266,7 +266,7 @@ def test_force_gather_row_residues(precision, n):
 
 def test_fp32_factor_runs_longer_than_one_recurrence():
     """FP32 boxes of more than 64 points per axis: the 1D factors are built in several runs of
-    the FP64 ratio recurrence (each restarted from exponentials); rho, V_H and the forces still
+    the ratio recurrence (each restarted from exponentials); rho, V_H and the forces still
     match the oracle.  Cell 6 x 6.25 x 7 Bohr on 96 x 100 x 112 (h = 0.0625 Bohr), sigma 0.6 Bohr,
     5 sigma cutoff: 97 points per axis."""
     S = synth.random_system((96, 100, 112), (6.0, 6.25, 7.0), 6, 0.6, seed=4242, precision="fp32")
