@@ -132,6 +132,19 @@ def test_full_step_matches_oracle(name, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_leaf_larger_than_the_setup_block(precision):
+    """All 64 atoms of config 2 in one leaf: the setup kernel's (atom, axis) tasks (192) and its
+    per-atom binning warps take several rounds of its 128 threads."""
+    S, ref = oracle_cfg("cfg2")
+    g = gpu_step(S, precision, atoms_per_leaf=64, max_atoms=64)
+    tol = TOL[precision]
+    assert rel_l2(g["rho"], ref["rho"]) <= tol["v"]
+    assert rel_l2(g["vh"], ref["vh"]) <= tol["v"]
+    assert abs(g["eh"] - ref["eh"]) <= tol["e"] * abs(ref["eh"])
+    assert np.max(np.abs(g["forces"] - ref["forces"])) <= tol["f"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_bisection_order_changes_nothing(precision):
     S, ref = oracle_cfg("cfg2")
     perm, _ = atoms_reorder(S.pos, 4)
